@@ -1,0 +1,407 @@
+"""Benchmark of the LSH indexing hot path on GB300 (one JSON line on rank 0).
+
+Step = one pass of the whole indexing path over one batch: CS/HCS hashing of
+all L tables (with the FP64 boundary recheck and key fold) -> per-table
+stable radix sort of (key, id) -> bucket segmentation, i.e. lsh_index_rebuild
+on a resident batch.  Workload (default): 1,000,000 x 960 FP32 points from a
+64-component Gaussian mixture (the Gist-shaped set), CS-E2LSH, m = 64, L = 50,
+w = 4.  Inputs (3.84 GB) are larger than L2 (129 MB), so no flush is needed.
+
+value  = points indexed per second over all ranks (weak scaling: each rank
+         indexes its own batch; no data-path collective).
+e2e    = the same through the public API with host buffers: pinned host X ->
+         device, rebuild, device -> host read of the per-table bucket counts.
+roofline = the dominant kernel (the CS/HCS hashing kernel) timed alone with
+         CUDA events on its stream.
+cpu_baseline = the FP64 oracle on a bounded sample of the same workload, on
+         the host cores (rank 0, N = 1 only).
+
+--impl reference runs that oracle as the reference arm (host cores only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hashed pts/s & HBM roofline %, CS/HCS vs dense; serve QPS, p99 @recall10≥0.9"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines = []
+        self.window = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, ln in self.lines:
+            if not (t0 - 0.15 <= ts <= t1 + 0.15):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel_key: str, workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    if it was taken on the current source of that kernel (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel_key]
+    except Exception:
+        return None
+    if rec.get("workload") != workload:
+        return None
+    if rec.get("source_sha") != _source_sha(rec.get("sources", [])):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def _workload(name, kind):
+    from paper_2503_06737_gb300 import workloads
+    wl = dict(workloads.WORKLOADS[name])
+    hcs = kind.startswith("hcs")
+    fam = dict(kind=kind, d=wl["d"], m=wl["m"], L=wl["L"], w=wl.get("w", 4.0), seed=42,
+               dims=wl["hcs_dims"] if hcs else None, mdims=wl["hcs_mdims"] if hcs else None)
+    return wl, fam
+
+
+def _make_X(wl, seed, device):
+    import torch
+    from paper_2503_06737_gb300 import workloads
+    dt = workloads.torch_dtype(wl.get("dtype", "f32"))
+    if wl["gen"] == "gmm":
+        return workloads.gmm(wl["n"], wl["d"], wl["components"], seed=seed, device=device, dtype=dt)
+    return workloads.iid(wl["n"], wl["d"], seed=seed, device=device, dtype=dt)
+
+
+def _oracle_setup(wl, fam_args, seed=1235):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2503_06737_gb300 import workloads
+    of = oracle.family(fam_args["kind"], fam_args["d"], fam_args["m"], fam_args["L"], w=fam_args["w"],
+                       seed=fam_args["seed"], dims=fam_args["dims"], mdims=fam_args["mdims"])
+    dt = workloads.torch_dtype(wl.get("dtype", "f32"))
+
+    def sample(rows):
+        X = workloads.gmm(rows, wl["d"], wl["components"], seed=seed, device="cpu", dtype=dt) \
+            if wl["gen"] == "gmm" else workloads.iid(rows, wl["d"], seed=seed, device="cpu", dtype=dt)
+        Xc = X.contiguous()
+        if Xc.dtype == torch.float32:
+            return Xc.numpy(), oracle.F32
+        return Xc.view(torch.int16).numpy().view(np.uint16), {torch.bfloat16: oracle.BF16,
+                                                             torch.float16: oracle.F16}[Xc.dtype]
+
+    def step(Xh, dtc):
+        """One oracle step on a sample: FP64 hash of every table, then the index."""
+        t = time.perf_counter()
+        st, _, _, keys = oracle.hash_dense(of, Xh, dtype=dtc, want_y=False, want_codes=False)
+        oracle.build_index(keys)
+        return time.perf_counter() - t
+
+    def calibrate(target_s):
+        rows = 256
+        Xh, dtc = sample(rows)
+        t = step(Xh, dtc)
+        rows = int(min(wl["n"], max(rows, rows * target_s / max(t, 1e-3))))
+        return rows, sample(rows)
+
+    return step, calibrate, oracle.num_threads()
+
+
+def oracle_sample_rate(wl, fam_args, target_s=15.0):
+    """Points/s of the oracle (hash + index) on a bounded sample, host cores."""
+    step, calibrate, cores = _oracle_setup(wl, fam_args)
+    rows, (Xh, dtc) = calibrate(target_s)
+    t = step(Xh, dtc)
+    return rows / t, rows, t, cores
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores; each
+    step hashes and indexes a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, fam_args = _workload(args.workload, args.kind)
+    step, calibrate, cores = _oracle_setup(wl, fam_args)
+    rows, (Xh, dtc) = calibrate(max(0.5, 90.0 / (args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        step(Xh, dtc)
+    ts = [step(Xh, dtc) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    rate = rows / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "kind": fam_args["kind"], "n_per_gpu": wl["n"], "d": wl["d"],
+                   "m": fam_args["m"], "L": fam_args["L"], "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows} rows of {args.workload} per step ({fam_args['kind']} hash + index)"},
+        "e2e": {"value": rate, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gmm64_1M_d960")
+    ap.add_argument("--kind", default="cs_e2lsh")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-family hashing lines")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_06737_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2503_06737_gb300 import lsh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    peaks, peak_src = _peaks()
+    wl, fam_args = _workload(args.workload, args.kind)
+    n, d, L, m = wl["n"], wl["d"], fam_args["L"], fam_args["m"]
+    X = _make_X(wl, seed=1235 + rank, device=dev)
+    fam = lsh.Family(**fam_args)
+    idx = fam.build_index(X, keep_data=False)
+    mtx = lsh.dense_matrix(X)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        idx.rebuild_into(mtx)
+    barrier()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sel = f"GPU-{uuid}" if uuid is not None else os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+    clocks = ClockSampler(sel)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = lsh.launch_count()
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        idx.rebuild_into(mtx)
+    e1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    launches = lsh.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n / (ms / 1e3)
+
+    # ---- dominant kernel alone: the hashing launch (keys only) ----
+    keys = torch.empty((L, n), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        fam.hash_into(mtx, None, lsh._ptr(keys), None)
+    barrier()
+    kst = max(10, args.steps // 2)
+    e0.record(stream)
+    for _ in range(kst):
+        fam.hash_into(mtx, None, lsh._ptr(keys), None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hash_ms = e0.elapsed_time(e1) / kst
+    adds = float(n) * d * L                     # signed adds: one per (coordinate, table)
+    bytes_alg = float(n) * d * X.element_size() + float(n) * L * 8
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = props.multi_processor_count
+    alu_peak = nsm * 128 * sm_max * 1e6 / 1e12  # FP32 adds/s in T/s
+    achieved = adds / (hash_ms / 1e3) / 1e12
+    traffic = _profiled_traffic("sketch_dense_kernel", args.workload)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "kernel": "sketch_dense_kernel (CS/HCS hash, all tables, keys only)",
+                "kernel_ms": hash_ms, "peak_source": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                "hbm_view": {"algorithmic_bytes": bytes_alg,
+                             "achieved_gbs": bytes_alg / (hash_ms / 1e3) / 1e9,
+                             "peak_gbs": peaks["hbm_gbs"],
+                             "frac": bytes_alg / (hash_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                             "peak_source": peak_src}}
+    t_wall2 = time.time()
+
+    # ---- end to end through the public API with host buffers ----
+    Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+    Xh.copy_(X)
+    nb_host = torch.empty(L, dtype=torch.int64, pin_memory=True)
+    Xd = torch.empty_like(X)
+    mtx_d = lsh.dense_matrix(Xd)
+    import ctypes
+    e2e_steps = max(5, args.steps // 5)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        idx.rebuild_into(mtx_d)
+        # the step's result: bucket counts of every table
+        lsh._check(lsh.lib().lsh_index_info(idx.handle, None, ctypes.c_void_p(nb_host.data_ptr())))
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "points/s",
+           "h2d_bytes_per_step": int(X.numel() * X.element_size()), "d2h_bytes_per_step": int(L * 8),
+           "ms_per_step": e2e_ms}
+    del Xh, Xd
+
+    # ---- per-family hashing throughput (keys only), same workload ----
+    variants = {}
+    if not args.no_extras:
+        for kind in ("cs_e2lsh", "hcs_e2lsh", "cs_srp", "hcs_srp"):
+            _, fa = _workload(args.workload, kind)
+            f2 = lsh.Family(**fa)
+            for _ in range(3):
+                f2.hash_into(mtx, None, lsh._ptr(keys), None)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                f2.hash_into(mtx, None, lsh._ptr(keys), None)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kms = e0.elapsed_time(e1) / 10
+            st = f2.hash(X, keys=True, stats=True)["stats"]
+            variants[kind] = {"hash_ms": kms, "points_per_s": n / (kms / 1e3),
+                              "alu_frac": adds / (kms / 1e3) / 1e12 / alu_peak,
+                              "hbm_frac": bytes_alg / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                              "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
+                              "changed": st["n_changed"]}
+            f2.close()
+    clocks.stop()
+    clk = clocks.summary(t_wall0, t_wall2)
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, rows, t, cores = oracle_sample_rate(wl, fam_args, target_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": f"{rows} rows of {args.workload}: {fam_args['kind']} hash + index, FP64, {t:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "kind": fam_args["kind"], "n_per_gpu": n, "d": d,
+                       "m": m, "L": L, "w": fam_args["w"],
+                       "step": "lsh_index_rebuild: hash (FP32 + FP64 recheck) + radix sort + buckets",
+                       "l2": "inputs larger than L2 (%.2f GB per GPU)" % (X.numel() * X.element_size() / 1e9)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

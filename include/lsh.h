@@ -1,0 +1,277 @@
+/*
+ * lsh.h -- C ABI of the GB300 (sm_103a) CS/HCS LSH hashing and indexing library.
+ *
+ * Paper: "Faster and Space Efficient Indexing for Locality Sensitive Hashing"
+ * (arXiv 2503.06737).  The library computes, for n points and L tables, the
+ * m-dimensional hashcodes of
+ *   - CS-E2LSH   (Definition 12, Sec. 4.1)  floor((sqrt(m) CS(x)_l + b_l) / w)
+ *   - HCS-E2LSH  (Definition 19, Sec. 4.2)  floor((sqrt(m) vec(HCS(x))_l + b_l) / w)
+ *   - CS-SRP     (Definition 25, Sec. 5.1)  1[CS(x)_l > 0]
+ *   - HCS-SRP    (Definition 31, Sec. 5.2)  1[vec(HCS(x))_l > 0]
+ * and of the dense baselines they replace,
+ *   - E2LSH      (Definition 2, Sec. 3.1)   floor((<r_l, x> + b_l) / w)
+ *   - SRP        (Definition 3, Sec. 3.1)   1[<r_l, x> > 0]
+ * where CS is the count sketch of Definition 4 and HCS the higher-order count
+ * sketch of Definition 5 (input viewed as a d_1 x ... x d_N tensor, first mode
+ * fastest, zero-padded when prod d_k > d, Sec. 6).  It groups the points into
+ * the L hash tables of the (m, tau)-amplified LSH scheme of Sec. 3.1 and
+ * answers queries by probing the L tables, taking the union of the buckets
+ * and ranking it by exact distance (Sec. 6).
+ *
+ * Integer results (codes, keys, bucket tables) are exact: the FP32 fast path
+ * carries a rigorous error bound, and every entry whose FP32 value lies within
+ * that bound of an E2LSH bin edge (or of 0 for SRP) is recomputed in FP64 in
+ * ascending coordinate order, one IEEE rounding per operation, which is the
+ * canonical result.
+ *
+ * Conventions for every call:
+ *   - Pointers named in the argument lists as "device" are CUDA device
+ *     pointers owned by the caller; "host" pointers are ordinary memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered and asynchronous unless a stats or export
+ *     argument is given, in which case they synchronise `stream` before
+ *     returning.
+ *   - Every call returns an lsh_status; no C++ exception crosses the ABI.
+ *     On failure lsh_last_error() returns a message for the calling thread.
+ *   - Handles are immutable after creation except for a sticky device status
+ *     word (lsh_family_status); concurrent calls on different streams that use
+ *     the same handle are safe.
+ */
+#ifndef LSH_GB300_H
+#define LSH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSH_OK = 0,
+  LSH_EINVAL = 1,        /* invalid argument (checked on the host before any launch) */
+  LSH_ENOMEM = 2,        /* device or host allocation failed */
+  LSH_ECUDA = 3,         /* a CUDA runtime call failed */
+  LSH_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  LSH_ENONFINITE = 5,    /* an input row held NaN or Inf: its codes and keys are not defined */
+  LSH_EUNSUPPORTED = 6,  /* valid request this build does not implement */
+  LSH_ERANGE = 7         /* an E2LSH code fell outside int32 */
+} lsh_status;
+
+/* Hash kinds (numbering fixed: it is part of the ABI). */
+typedef enum {
+  LSH_E2LSH = 0,      /* dense Gaussian projection, floor       (Definition 2)  */
+  LSH_SRP = 1,        /* dense Gaussian projection, sign        (Definition 3)  */
+  LSH_CS_E2LSH = 2,   /* count sketch, scaled floor             (Definition 12) */
+  LSH_HCS_E2LSH = 3,  /* higher-order count sketch, scaled floor (Definition 19) */
+  LSH_CS_SRP = 4,     /* count sketch, sign                     (Definition 25) */
+  LSH_HCS_SRP = 5     /* higher-order count sketch, sign        (Definition 31) */
+} lsh_kind;
+
+/* Element types of inputs. */
+typedef enum {
+  LSH_F32 = 0,
+  LSH_BF16 = 1,
+  LSH_F16 = 2,
+  LSH_FP8_E4M3 = 3   /* OCP E4M3 (finite-only variant) with a per-row FP32 scale */
+} lsh_dtype;
+
+#define LSH_MAX_MODES 8
+
+/*
+ * Family description.  The family is drawn from `seed` on the host:
+ * per table t, SplitMix64 (Steele, Lea & Flood 2014) started at
+ * mix64(seed + (t+1) * 0x9E3779B97F4A7C15) gives, in this order,
+ *   for each mode k, each i < dims[k]: bin = (hi32(r) * mdims[k]) >> 32,
+ *                                      sign = bit31(r) ? -1 : +1;
+ *   (dense kinds instead: G[j][t*m + l] for j < d, l < m by Box-Muller on
+ *    two draws, stored as FP32);
+ *   b_l = w * hi53(r) * 2^-53 for l < m;
+ *   key multipliers ka_l = hi32(r) | 1, kb_l = lo32(r) | 1 for l < m.
+ *
+ *   kind    lsh_kind.
+ *   d       input dimension (>= 1).
+ *   m       code length per table (bins per table), >= 1; = prod mdims.
+ *   L       number of tables, >= 1.
+ *   N       number of HCS modes (1 <= N <= LSH_MAX_MODES); CS kinds: 1.
+ *   dims    HCS mode sizes, prod dims >= d (zero padding beyond d); CS: {d}.
+ *   mdims   HCS sketch sizes per mode, prod = m; CS: {m}.
+ *   w       E2LSH bin width (> 0; ignored by SRP kinds, still drawn).
+ *   seed    64-bit family seed.
+ *   compute element type the dense kinds store G in (LSH_F32 today).
+ */
+typedef struct {
+  int32_t kind;
+  int32_t d;
+  int32_t m;
+  int32_t L;
+  int32_t N;
+  int32_t dims[LSH_MAX_MODES];
+  int32_t mdims[LSH_MAX_MODES];
+  double w;
+  uint64_t seed;
+  int32_t compute;
+} lsh_family_desc;
+
+/*
+ * A batch of points (device memory, caller-owned, read-only during the call).
+ *   dense: values = [n][ld] elements of `dtype` row-major, col = rowptr = NULL.
+ *   CSR:   rowptr = [n+1] int64 offsets, col = [nnz] int32 column indices,
+ *          strictly ascending within a row and < d; values = [nnz] FP32.
+ *   row_scale: FP8 inputs only, [n] FP32, x[i][j] = row_scale[i] * q[i][j].
+ */
+typedef struct {
+  int32_t dtype;
+  int64_t n;
+  int64_t d;
+  int64_t ld;
+  const void *values;
+  const int32_t *col;
+  const int64_t *rowptr;
+  const float *row_scale;
+} lsh_matrix;
+
+typedef struct lsh_family_s *lsh_family_t;
+typedef struct lsh_index_s *lsh_index_t;
+
+/* Counters of one lsh_hash call (filled only when a stats pointer is given). */
+typedef struct {
+  int64_t n_entries;    /* n * L * m discretised entries */
+  int64_t n_flagged;    /* entries within the FP32 error margin, recomputed in FP64 */
+  int64_t n_changed;    /* of those, entries whose FP64 code differs from the FP32 one */
+  int64_t n_nonfinite;  /* rows holding NaN or Inf */
+  int64_t n_overflow;   /* E2LSH codes outside int32 */
+} lsh_hash_stats;
+
+typedef struct {
+  int64_t n_queries;
+  int64_t n_candidates;        /* sum over queries of the bucket-union sizes (with repeats) */
+  int64_t n_unique;            /* sum over queries of distinct candidates */
+  int64_t max_unique;          /* largest distinct-candidate count of one query */
+} lsh_query_stats;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *lsh_last_error(void);
+
+/* Library version string. */
+const char *lsh_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (for accounting of launches inside a timed region). */
+uint64_t lsh_launch_count(void);
+
+/*
+ * Draw a family (Definitions 2-5) and upload its tables to the current device.
+ *   desc  host pointer, validated (LSH_EINVAL on any inconsistency).
+ *   out   host pointer receiving the handle; the handle owns device memory
+ *         until lsh_family_destroy.
+ */
+lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out);
+
+/*
+ * Draw the tables of the family `desc` on the host only (no device use) into
+ * host buffers laid out as in lsh_family_export (any may be NULL).  For
+ * checking the sampler against an independent implementation without a GPU.
+ */
+lsh_status lsh_sample_family_tables(const lsh_family_desc *desc, int32_t *bins, int8_t *signs, float *G,
+                                    double *b, uint32_t *ka, uint32_t *kb);
+
+/* Copy the description of a family into *desc (host). */
+lsh_status lsh_family_describe(lsh_family_t fam, lsh_family_desc *desc);
+
+/*
+ * Copy the family's tables to host buffers (any may be NULL):
+ *   bins   [L][sum dims] int32   per-mode bucket hashes h_k, modes concatenated
+ *   signs  [L][sum dims] int8    per-mode signs s_k
+ *   G      [d][m*L] float        dense kinds only
+ *   b      [L][m] double         E2LSH offsets
+ *   ka, kb [L][m] uint32         key multipliers
+ * Synchronous.  For parity checks against an independent implementation.
+ */
+lsh_status lsh_family_export(lsh_family_t fam, int32_t *bins, int8_t *signs, float *G,
+                             double *b, uint32_t *ka, uint32_t *kb);
+
+/*
+ * Read (and optionally clear) the family's sticky device status: bit 0 set
+ * when some row was not finite, bit 1 when some code overflowed int32 in a
+ * call made without stats.  Synchronises the device.
+ */
+lsh_status lsh_family_status(lsh_family_t fam, int32_t *status, int32_t clear);
+
+void lsh_family_destroy(lsh_family_t fam);
+
+/*
+ * Hash the rows of X for all L tables in one launch (Definitions 2, 3, 12,
+ * 19, 25, 31).
+ *   X      host pointer to the batch description; its arrays are device memory;
+ *          X->d must equal the family's d.  Dense inputs: f32/bf16/f16 for the
+ *          CS/HCS kinds.  CSR inputs: CS/HCS kinds.
+ *   codes  device, optional: E2LSH kinds int32 [n][L][m]; SRP kinds uint64
+ *          [n][L][ceil(m/64)] with code l in bit (l % 64) of word l / 64.
+ *   keys   device, optional: uint64 [L][n], the bucket key of (point, table):
+ *          SRP with m <= 64: the code bits; otherwise
+ *          (sum_l code_l ka_l mod 2^32) * 2^32 + (sum_l code_l kb_l mod 2^32).
+ *   proj   device, optional: float [n][L][m], the FP32 projection (sqrt(m) not
+ *          applied), for error reporting.
+ *   stats  host, optional: if given the call synchronises and fills it, and
+ *          returns LSH_ENONFINITE / LSH_ERANGE when such rows/codes occurred.
+ * Rows that hold NaN/Inf get key 0xFFFFFFFFFFFFFFFF and code INT32_MIN.
+ */
+lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys,
+                    float *proj, lsh_hash_stats *stats, void *stream);
+
+/*
+ * Build the L hash tables of Sec. 3.1 over X: hash (keys only), then per
+ * table a stable device radix sort of (key, id) and the bucket segmentation.
+ *   keep_data  nonzero: the index keeps a device copy of X (dense rows) for
+ *              lsh_query's exact rerank; zero: it keeps only the tables.
+ *   out        host pointer receiving the handle (owns its device memory).
+ * Stream-ordered; the caller may free X once `stream` has passed the call.
+ */
+lsh_status lsh_build_index(lsh_family_t fam, const lsh_matrix *X, int32_t keep_data,
+                           lsh_index_t *out, void *stream);
+
+/*
+ * Rebuild an existing index over a new batch X with the same n (and d): hash,
+ * sort and segment into the index's own arrays; when the index keeps data the
+ * copy of X is refreshed too.  Stream-ordered; no device allocation beyond the
+ * per-call temporaries of the sort (stream-ordered pool).
+ */
+lsh_status lsh_index_rebuild(lsh_index_t idx, const lsh_matrix *X, void *stream);
+
+/* n and, for each table, the number of buckets (host, [L]; may be NULL).  Synchronous. */
+lsh_status lsh_index_info(lsh_index_t idx, int64_t *n, int64_t *nbuckets);
+
+/*
+ * Copy the tables to host buffers (any may be NULL):
+ *   ids      [L][n] uint32   point ids ordered by (key, id)
+ *   ukeys    [L][n] uint64   distinct keys, ascending (first nbuckets[t] valid)
+ *   offsets  [L][n+1] uint32 bucket starts in ids, offsets[t][nbuckets[t]] = n
+ *   nbuckets [L] int64
+ * Synchronous.
+ */
+lsh_status lsh_index_export(lsh_index_t idx, uint32_t *ids, uint64_t *ukeys, uint32_t *offsets,
+                            int64_t *nbuckets);
+
+/*
+ * Answer a batch of queries (Sec. 3.1 probe, Sec. 6 rerank): hash each query,
+ * look its key up in every table, take the union of those buckets, rank the
+ * distinct candidates by exact distance (Euclidean for E2LSH kinds, cosine
+ * distance 1 - cos for SRP kinds; FP32 arithmetic) and return the k best by
+ * (distance, id).  Needs an index built with keep_data.
+ *   Q     host pointer to a dense batch (device arrays), same dtype as the index data.
+ *   k     1 <= k <= 256.
+ *   ids   device int32 [q][k], -1 where fewer than k candidates exist.
+ *   dist  device float [q][k], +inf there.
+ *   stats host, optional (synchronises).
+ */
+lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *ids, float *dist,
+                     lsh_query_stats *stats, void *stream);
+
+void lsh_index_destroy(lsh_index_t idx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSH_GB300_H */

@@ -1,0 +1,95 @@
+// family.cpp -- host sampler of the LSH family (the random functions of
+// Definitions 2-5: per-mode h_k, s_k; dense Gaussian projection; offsets b;
+// key multipliers), drawn from a 64-bit seed with SplitMix64 (Steele, Lea &
+// Flood, OOPSLA 2014).  Compiled with -ffp-contract=off so the Box-Muller
+// arithmetic is one IEEE rounding per operation.
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace lsh {
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+inline uint64_t finalize(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// A SplitMix64 stream: Weyl state advanced by the golden gamma, output mixed.
+class Stream {
+ public:
+  Stream(uint64_t seed, int table) : state_(finalize(seed + uint64_t(table + 1) * kGamma)) {}
+  uint64_t next() {
+    state_ += kGamma;
+    return finalize(state_);
+  }
+
+ private:
+  uint64_t state_;
+};
+
+inline double unit53(uint64_t r) { return double(r >> 11) * 0x1.0p-53; }
+
+void draw_offsets_and_keys(Stream &s, const lsh_family_desc &d, int t, HostFamily &hf) {
+  const int m = d.m;
+  for (int l = 0; l < m; ++l) hf.b[size_t(t) * m + l] = d.w * unit53(s.next());
+  for (int l = 0; l < m; ++l) {
+    uint64_t r = s.next();
+    hf.ka[size_t(t) * m + l] = uint32_t(r >> 32) | 1u;
+    hf.kb[size_t(t) * m + l] = uint32_t(r) | 1u;
+  }
+}
+
+}  // namespace
+
+void sample_family(const lsh_family_desc &d, HostFamily &hf) {
+  hf.desc = d;
+  const int L = d.L, m = d.m;
+  hf.b.assign(size_t(L) * m, 0.0);
+  hf.ka.assign(size_t(L) * m, 0u);
+  hf.kb.assign(size_t(L) * m, 0u);
+  if (kind_is_dense(d.kind)) {
+    hf.dsum = 0;
+    const size_t ldg = size_t(m) * L;
+    hf.G.assign(size_t(d.d) * ldg, 0.f);
+    const double two_pi = 6.283185307179586;
+    for (int t = 0; t < L; ++t) {
+      Stream s(d.seed, t);
+      for (int j = 0; j < d.d; ++j)
+        for (int l = 0; l < m; ++l) {
+          const uint64_t r1 = s.next(), r2 = s.next();
+          const double u1 = double((r1 >> 11) + 1) * 0x1.0p-53;  // (0, 1]
+          const double u2 = double(r2 >> 11) * 0x1.0p-53;        // [0, 1)
+          const double radius = std::sqrt(-2.0 * std::log(u1));
+          const double g = radius * std::cos(two_pi * u2);
+          hf.G[size_t(j) * ldg + size_t(t) * m + l] = float(g);
+        }
+      draw_offsets_and_keys(s, d, t, hf);
+    }
+    return;
+  }
+  int64_t dsum = 0;
+  for (int k = 0; k < d.N; ++k) dsum += d.dims[k];
+  hf.dsum = dsum;
+  hf.bins.assign(size_t(L) * dsum, 0);
+  hf.signs.assign(size_t(L) * dsum, 1);
+  for (int t = 0; t < L; ++t) {
+    Stream s(d.seed, t);
+    int64_t base = int64_t(t) * dsum;
+    for (int k = 0; k < d.N; ++k) {
+      const uint64_t mk = uint32_t(d.mdims[k]);
+      for (int i = 0; i < d.dims[k]; ++i, ++base) {
+        const uint64_t r = s.next();
+        hf.bins[base] = int32_t(((r >> 32) * mk) >> 32);
+        hf.signs[base] = (r & (1ULL << 31)) ? int8_t(-1) : int8_t(1);
+      }
+    }
+    draw_offsets_and_keys(s, d, t, hf);
+  }
+}
+
+}  // namespace lsh

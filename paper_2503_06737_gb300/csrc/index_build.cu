@@ -1,0 +1,294 @@
+// index_build.cu -- the L hash tables of the (m, tau)-amplified LSH scheme
+// (Sec. 3.1): every point is stored in the bucket of its key in each table.
+//
+// Per table the (key, id) pairs are put in (key, id) order by a stable LSD
+// radix sort over the 64-bit key, 8 bits per pass (ids start in ascending
+// order, so stability gives ascending ids inside a bucket), and the sorted
+// keys are cut into buckets: distinct keys ascending and the start offset of
+// each bucket.  All L tables are sorted by the same launches (grid.y = table).
+//
+// One pass = three kernels:
+//   histogram  per (table, tile of 4096 keys): digit counts, digit-major;
+//   scan       per table: exclusive scan over (digit, tile) -> global offsets;
+//   scatter    per (table, tile): stable ranks inside the tile from warp
+//              match-any over 32 consecutive keys at a time, warp-ordered
+//              prefix, sorted tile staged in shared memory, then written out
+//              in order (runs of one digit land contiguously).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace lsh {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;                    // keys per thread
+constexpr int kTile = kThreads * kItems;      // 4096 keys per tile
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) {
+  return uint32_t(k >> shift) & (kRadix - 1);
+}
+
+__global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                       int shift, int ntiles, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[kWarps][kRadix];
+  const int t = blockIdx.y, tile = blockIdx.x;
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const uint64_t *k = keys + int64_t(t) * n;
+  const int64_t base = int64_t(tile) * kTile;
+  for (int i = threadIdx.x; i < kTile; i += kThreads) {
+    const int64_t idx = base + i;
+    if (idx < n) atomicAdd(&h[warp][digit_of(k[idx], shift)], 1u);
+  }
+  __syncthreads();
+  for (int dgt = threadIdx.x; dgt < kRadix; dgt += kThreads) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += h[w][dgt];
+    hist[(int64_t(t) * kRadix + dgt) * ntiles + tile] = s;
+  }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x = 1024).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_sums, uint32_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += u;
+  }
+  if (lane == 31) warp_sums[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+    uint32_t ws = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += u;
+    }
+    if (lane < nw) warp_sums[lane] = ws - w;
+    if (lane == 31) warp_sums[32] = ws;
+  }
+  __syncthreads();
+  const uint32_t r = warp_sums[warp] + s - v;
+  total = warp_sums[32];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive scan, in place, of cnt[t][0..len) for each table t (grid.x = table).
+// Optionally writes the table total to total_out[t].
+__global__ void __launch_bounds__(1024) scan_rows(uint32_t *__restrict__ cnt, int64_t len,
+                                                  int64_t *__restrict__ total_out) {
+  __shared__ uint32_t warp_sums[33];
+  uint32_t *c = cnt + int64_t(blockIdx.x) * len;
+  const int64_t per = (len + blockDim.x - 1) / blockDim.x;
+  const int64_t beg = int64_t(threadIdx.x) * per;
+  const int64_t end = beg + per < len ? beg + per : len;
+  uint32_t s = 0;
+  for (int64_t i = beg; i < end; ++i) s += c[i];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, warp_sums, total);
+  for (int64_t i = beg; i < end; ++i) {
+    const uint32_t v = c[i];
+    c[i] = run;
+    run += v;
+  }
+  if (total_out && threadIdx.x == 0) total_out[blockIdx.x] = int64_t(total);
+}
+
+__global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__restrict__ kin,
+                                                          const uint32_t *__restrict__ iin,
+                                                          uint64_t *__restrict__ kout,
+                                                          uint32_t *__restrict__ iout, int64_t n, int shift,
+                                                          int ntiles, const uint32_t *__restrict__ gscan) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(sm);                       // [kTile]
+  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kTile);               // [kTile]
+  uint32_t *wc = si + kTile;                                             // [kWarps][kRadix]
+  uint32_t *dstart = wc + kWarps * kRadix;                               // [kRadix]
+  uint32_t *gbase = dstart + kRadix;                                     // [kRadix]
+  uint32_t *wsum = gbase + kRadix;                                       // [33]
+
+  const int t = blockIdx.y, tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t *k = kin + int64_t(t) * n;
+  const uint32_t *ids = iin ? iin + int64_t(t) * n : nullptr;
+  const int64_t base = int64_t(tile) * kTile;
+  const int64_t cnt64 = n - base < kTile ? n - base : kTile;
+  const int count = int(cnt64);
+
+  for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) wc[i] = 0;
+  __syncthreads();
+
+  // warp w owns keys [w*512, (w+1)*512) of the tile, 32 consecutive per round
+  uint64_t key[kItems];
+  uint32_t id[kItems];
+  uint32_t rank[kItems];
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t *mycnt = wc + warp * kRadix;
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int pos = warp * (kItems * 32) + it * 32 + lane;
+    const bool act = pos < count;
+    key[it] = act ? k[base + pos] : ~0ull;
+    id[it] = act ? (ids ? ids[base + pos] : uint32_t(base + pos)) : 0u;
+    const uint32_t dg = act ? digit_of(key[it], shift) : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t r = 0;
+    if (act) r = mycnt[dg] + __popc(peers & lt);
+    __syncwarp();
+    if (act && (peers & lt) == 0) mycnt[dg] += __popc(peers);
+    __syncwarp();
+    rank[it] = r;
+  }
+  __syncthreads();
+  // per digit: prefix over warps; totals; block-local digit starts
+  {
+    const int dgt = threadIdx.x;  // kThreads == kRadix
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = wc[w * kRadix + dgt];
+      wc[w * kRadix + dgt] = run;
+      run += c;
+    }
+    uint32_t tot;
+    const uint32_t st = block_exclusive_scan(run, wsum, tot);
+    dstart[dgt] = st;
+    gbase[dgt] = gscan[(int64_t(t) * kRadix + dgt) * ntiles + tile];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int pos = warp * (kItems * 32) + it * 32 + lane;
+    if (pos < count) {
+      const uint32_t dg = digit_of(key[it], shift);
+      const uint32_t p = dstart[dg] + wc[warp * kRadix + dg] + rank[it];
+      sk[p] = key[it];
+      si[p] = id[it];
+    }
+  }
+  __syncthreads();
+  uint64_t *ko = kout + int64_t(t) * n;
+  uint32_t *io = iout + int64_t(t) * n;
+  for (int s = threadIdx.x; s < count; s += kThreads) {
+    const uint64_t kk = sk[s];
+    const uint32_t dg = digit_of(kk, shift);
+    const int64_t g = int64_t(gbase[dg]) + (s - int64_t(dstart[dg]));
+    ko[g] = kk;
+    io[g] = si[s];
+  }
+}
+
+// Segmentation: bucket heads of sorted keys.
+__global__ void __launch_bounds__(kThreads) seg_count(const uint64_t *__restrict__ sk, int64_t n, int ntiles,
+                                                      uint32_t *__restrict__ bcnt) {
+  __shared__ uint32_t wsum[33];
+  const int t = blockIdx.y, tile = blockIdx.x;
+  const uint64_t *k = sk + int64_t(t) * n;
+  const int64_t base = int64_t(tile) * kTile;
+  uint32_t c = 0;
+  for (int i = threadIdx.x; i < kTile; i += kThreads) {
+    const int64_t idx = base + i;
+    if (idx < n && (idx == 0 || k[idx] != k[idx - 1])) ++c;
+  }
+  uint32_t tot;
+  block_exclusive_scan(c, wsum, tot);
+  if (threadIdx.x == 0) bcnt[int64_t(t) * ntiles + tile] = tot;
+}
+
+__global__ void __launch_bounds__(kThreads) seg_write(const uint64_t *__restrict__ sk, int64_t n, int ntiles,
+                                                      const uint32_t *__restrict__ boffs,
+                                                      const int64_t *__restrict__ nb,
+                                                      uint64_t *__restrict__ ukeys,
+                                                      uint32_t *__restrict__ offsets) {
+  __shared__ uint32_t wsum[33];
+  const int t = blockIdx.y, tile = blockIdx.x;
+  const uint64_t *k = sk + int64_t(t) * n;
+  const int64_t base = int64_t(tile) * kTile;
+  // contiguous chunk of kItems keys per thread keeps heads in order
+  const int64_t my = base + int64_t(threadIdx.x) * kItems;
+  uint32_t c = 0;
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t idx = my + it;
+    if (idx < n && (idx == 0 || k[idx] != k[idx - 1])) ++c;
+  }
+  uint32_t tot;
+  uint32_t pos = boffs[int64_t(t) * ntiles + tile] + block_exclusive_scan(c, wsum, tot);
+  uint64_t *uk = ukeys + int64_t(t) * n;
+  uint32_t *of = offsets + int64_t(t) * (n + 1);
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t idx = my + it;
+    if (idx < n && (idx == 0 || k[idx] != k[idx - 1])) {
+      uk[pos] = k[idx];
+      of[pos] = uint32_t(idx);
+      ++pos;
+    }
+  }
+  if (tile == 0 && threadIdx.x == 0) of[nb[t]] = uint32_t(n);
+}
+
+}  // namespace
+
+cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out, uint64_t *ukeys_out,
+                         uint32_t *offsets_out, int64_t *nb_out, cudaStream_t stream) {
+  if (L <= 0) return cudaSuccess;
+  if (n == 0) return cudaMemsetAsync(nb_out, 0, sizeof(int64_t) * L, stream);
+  const int ntiles = int((n + kTile - 1) / kTile);
+  const size_t nk = size_t(n) * L;
+  uint64_t *kA = nullptr, *kB = nullptr;
+  uint32_t *iA = nullptr, *hist = nullptr;
+  const size_t hist_len = size_t(kRadix) * ntiles;
+  cudaError_t e;
+  e = cudaMallocAsync(&kA, nk * 8, stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&kB, nk * 8, stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&iA, nk * 4, stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&hist, hist_len * L * 4, stream);
+  const int scatter_smem = kTile * 12 + (kWarps * kRadix + 2 * kRadix + 33) * 4;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem);
+  // 8 passes, ping-pong so that the last pass writes ids into ids_out:
+  // pass p reads (kin, iin) and writes (kout, iout).
+  const uint64_t *kin = keys;
+  const uint32_t *iin = nullptr;
+  for (int pass = 0; pass < 8 && e == cudaSuccess; ++pass) {
+    uint64_t *kout = (pass % 2 == 0) ? kA : kB;
+    uint32_t *iout = (pass % 2 == 0) ? iA : ids_out;
+    const dim3 grid((unsigned)ntiles, (unsigned)L);
+    radix_hist<<<grid, kThreads, 0, stream>>>(kin, n, pass * 8, ntiles, hist);
+    scan_rows<<<L, 1024, 0, stream>>>(hist, int64_t(hist_len), nullptr);
+    radix_scatter<<<grid, kThreads, scatter_smem, stream>>>(kin, iin, kout, iout, n, pass * 8, ntiles, hist);
+    e = cudaGetLastError();
+    count_launches(3);
+    kin = kout;
+    iin = iout;
+  }
+  // sorted keys in kB, ids in ids_out; buckets
+  if (e == cudaSuccess) {
+    const dim3 grid((unsigned)ntiles, (unsigned)L);
+    uint32_t *bcnt = hist;  // reuse: L * ntiles <= L * hist_len
+    seg_count<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, bcnt);
+    scan_rows<<<L, 1024, 0, stream>>>(bcnt, ntiles, nb_out);
+    seg_write<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, bcnt, nb_out, ukeys_out, offsets_out);
+    e = cudaGetLastError();
+    count_launches(3);
+  }
+  if (kA) cudaFreeAsync(kA, stream);
+  if (kB) cudaFreeAsync(kB, stream);
+  if (iA) cudaFreeAsync(iA, stream);
+  if (hist) cudaFreeAsync(hist, stream);
+  return e;
+}
+
+}  // namespace lsh

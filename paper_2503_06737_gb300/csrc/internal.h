@@ -1,0 +1,131 @@
+// internal.h -- library-internal declarations shared by the host runtime and
+// the CUDA kernels of the LSH library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lsh.h"
+
+namespace lsh {
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+lsh_status fail(lsh_status st, const std::string &msg);
+lsh_status cuda_fail(cudaError_t e, const char *what);
+
+#define LSH_CUDA_TRY(expr)                                         \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return ::lsh::cuda_fail(_e, #expr);     \
+  } while (0)
+
+// Kernel launch accounting (lsh_launch_count).
+void count_launches(uint64_t k);
+
+// Sticky device status bits (family status word).
+enum : uint32_t { STATUS_NONFINITE = 1u, STATUS_OVERFLOW = 2u };
+
+// Per-call device counters (order matches lsh_hash_stats after n_entries).
+enum { CNT_FLAGGED = 0, CNT_CHANGED = 1, CNT_NONFINITE = 2, CNT_OVERFLOW = 3, CNT_NUM = 8 };
+
+inline bool kind_is_srp(int k) { return k == LSH_SRP || k == LSH_CS_SRP || k == LSH_HCS_SRP; }
+inline bool kind_is_dense(int k) { return k == LSH_E2LSH || k == LSH_SRP; }
+inline bool kind_is_sketch(int k) { return !kind_is_dense(k); }
+inline bool kind_scaled(int k) { return k == LSH_CS_E2LSH || k == LSH_HCS_E2LSH; }
+
+// ---------------------------------------------------------------------------
+// Family: host copy of the drawn tables plus the device copies kernels read.
+// ---------------------------------------------------------------------------
+struct HostFamily {
+  lsh_family_desc desc;
+  int64_t dsum = 0;               // sum of mode sizes
+  std::vector<int32_t> bins;      // [L][dsum]
+  std::vector<int8_t> signs;      // [L][dsum]
+  std::vector<float> G;           // [d][m*L] dense kinds
+  std::vector<double> b;          // [L][m]
+  std::vector<uint32_t> ka, kb;   // [L][m]
+};
+
+// Draw every table of the family from its seed (host, deterministic).
+void sample_family(const lsh_family_desc &desc, HostFamily &hf);
+
+}  // namespace lsh
+
+struct lsh_family_s {
+  lsh::HostFamily host;
+  // device copies
+  uint16_t *d_bins = nullptr;     // [L][dsum] per-mode bins (< 65536)
+  int8_t *d_signs = nullptr;      // [L][dsum]
+  float *d_b32 = nullptr;         // [L][m] b rounded to FP32
+  double *d_b64 = nullptr;        // [L][m]
+  uint32_t *d_ka = nullptr;       // [L][m]
+  uint32_t *d_kb = nullptr;       // [L][m]
+  float *d_G = nullptr;           // [d][m*L] dense kinds
+  uint32_t *d_status = nullptr;   // sticky status word
+  int device = 0;
+};
+
+struct lsh_index_s {
+  lsh_family_t fam = nullptr;     // borrowed (the family must outlive the index)
+  int64_t n = 0;
+  int32_t L = 0;
+  uint32_t *d_ids = nullptr;      // [L][n]
+  uint64_t *d_ukeys = nullptr;    // [L][n]
+  uint32_t *d_offsets = nullptr;  // [L][n+1]
+  int64_t *d_nb = nullptr;        // [L]
+  void *d_data = nullptr;         // dense copy of X (optional)
+  int32_t data_dtype = 0;
+  int64_t data_ld = 0;
+  int64_t d = 0;
+};
+
+namespace lsh {
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns cudaSuccess or the launch error).
+// ---------------------------------------------------------------------------
+struct SketchLaunch {
+  // input
+  const void *X;
+  int32_t dtype;
+  int64_t n, ld;
+  int32_t d;
+  // family
+  int32_t kind, m, L, N;
+  int32_t dims[LSH_MAX_MODES], mdims[LSH_MAX_MODES];
+  int32_t dsum;
+  const uint16_t *bins;
+  const int8_t *signs;
+  const float *b32;
+  const double *b64;
+  const uint32_t *ka, *kb;
+  double w, sqrtm;
+  // outputs
+  int32_t *codes;        // E2LSH [n][L][m]
+  uint64_t *bits;        // SRP [n][L][words]
+  uint64_t *keys;        // [L][key_ld]
+  int64_t key_ld;
+  float *proj;           // [n][L][m]
+  unsigned long long *counters;  // CNT_NUM or nullptr
+  uint32_t *status;
+};
+
+// Dense-row CS/HCS hashing (all L tables, one launch).
+cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream);
+// Plan of the dense-row kernel for a shape (for reporting / autotuning).
+struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
+SketchPlan plan_sketch_dense(int d, int m, int L, int dtype);
+
+// Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
+// Allocates its temporaries with cudaMallocAsync on `stream`.
+cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
+                         uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out,
+                         cudaStream_t stream);
+
+}  // namespace lsh

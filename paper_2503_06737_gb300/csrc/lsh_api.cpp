@@ -1,0 +1,448 @@
+// lsh_api.cpp -- the C ABI of include/lsh.h: argument validation, handle
+// ownership, per-call temporaries and error reporting around the kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace lsh {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+lsh_status fail(lsh_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+lsh_status cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? LSH_ENOMEM : LSH_ECUDA;
+}
+
+namespace {
+
+lsh_status validate_desc(const lsh_family_desc &d) {
+  if (d.kind < LSH_E2LSH || d.kind > LSH_HCS_SRP) return fail(LSH_EINVAL, "unknown kind");
+  if (d.d < 1) return fail(LSH_EINVAL, "d must be >= 1");
+  if (d.m < 1) return fail(LSH_EINVAL, "m must be >= 1");
+  if (d.L < 1) return fail(LSH_EINVAL, "L must be >= 1");
+  if (!(d.w > 0.0) || !std::isfinite(d.w)) return fail(LSH_EINVAL, "w must be finite and > 0");
+  if (kind_is_dense(d.kind)) {
+    if (d.compute != LSH_F32) return fail(LSH_EUNSUPPORTED, "dense families store G in FP32 in this build");
+    if (int64_t(d.d) * d.m * d.L > (int64_t(1) << 31)) return fail(LSH_EINVAL, "G too large");
+    return LSH_OK;
+  }
+  if (d.N < 1 || d.N > LSH_MAX_MODES) return fail(LSH_EINVAL, "N must be in [1, 8]");
+  int64_t D = 1, M = 1;
+  for (int k = 0; k < d.N; ++k) {
+    if (d.dims[k] < 1 || d.mdims[k] < 1) return fail(LSH_EINVAL, "mode sizes must be >= 1");
+    if (d.mdims[k] > 65535) return fail(LSH_EINVAL, "mode sketch size must be < 65536");
+    D *= d.dims[k];
+    M *= d.mdims[k];
+    if (D > (int64_t(1) << 31) || M > (int64_t(1) << 31)) return fail(LSH_EINVAL, "modes too large");
+  }
+  if (M != d.m) return fail(LSH_EINVAL, "prod(mdims) must equal m");
+  if (D < d.d) return fail(LSH_EINVAL, "prod(dims) must be >= d");
+  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP) && (d.N != 1 || d.dims[0] != d.d))
+    return fail(LSH_EINVAL, "CS kinds take N = 1, dims = {d}, mdims = {m}");
+  if (d.m > 65535) return fail(LSH_EINVAL, "m must be < 65536");
+  return LSH_OK;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const T *src, size_t count) {
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_family(lsh_family_s *f) {
+  if (!f) return;
+  cudaFree(f->d_bins);
+  cudaFree(f->d_signs);
+  cudaFree(f->d_b32);
+  cudaFree(f->d_b64);
+  cudaFree(f->d_ka);
+  cudaFree(f->d_kb);
+  cudaFree(f->d_G);
+  cudaFree(f->d_status);
+  delete f;
+}
+
+lsh_status validate_matrix(const lsh_family_s *f, const lsh_matrix *X, bool allow_csr) {
+  if (!X) return fail(LSH_EINVAL, "X is NULL");
+  if (X->n < 0) return fail(LSH_EINVAL, "n must be >= 0");
+  if (X->n > int64_t(UINT32_MAX) - 1) return fail(LSH_EINVAL, "n must be < 2^32 - 1");
+  if (X->d != f->host.desc.d) return fail(LSH_EINVAL, "X->d differs from the family's d");
+  const bool csr = X->rowptr != nullptr;
+  if (csr) {
+    if (!allow_csr) return fail(LSH_EINVAL, "CSR input not accepted here");
+    if (X->n > 0 && (!X->col || !X->values)) return fail(LSH_EINVAL, "CSR needs col and values");
+    if (X->dtype != LSH_F32) return fail(LSH_EINVAL, "CSR values must be FP32");
+    return LSH_OK;
+  }
+  if (X->n > 0 && !X->values) return fail(LSH_EINVAL, "values is NULL");
+  if (X->ld < X->d) return fail(LSH_EINVAL, "ld must be >= d");
+  if (X->dtype != LSH_F32 && X->dtype != LSH_BF16 && X->dtype != LSH_F16 && X->dtype != LSH_FP8_E4M3)
+    return fail(LSH_EINVAL, "unknown dtype");
+  if (X->dtype == LSH_FP8_E4M3 && !X->row_scale) return fail(LSH_EINVAL, "FP8 input needs row_scale");
+  return LSH_OK;
+}
+
+size_t dtype_size(int dt) { return dt == LSH_F32 ? 4 : (dt == LSH_FP8_E4M3 ? 1 : 2); }
+
+// Hash into keys [L][key_ld] (and the optional outputs).  Stream-ordered.
+lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
+                     float *proj, unsigned long long *counters, cudaStream_t stream) {
+  const lsh_family_desc &d = f->host.desc;
+  if (X->n == 0) return LSH_OK;
+  if (kind_is_dense(d.kind)) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP hashing is not in this build yet");
+  if (X->rowptr) return fail(LSH_EUNSUPPORTED, "CSR hashing is not in this build yet");
+  if (X->dtype == LSH_FP8_E4M3) return fail(LSH_EUNSUPPORTED, "FP8 input is for the dense kinds");
+  SketchLaunch p{};
+  p.X = X->values;
+  p.dtype = X->dtype;
+  p.n = X->n;
+  p.ld = X->ld;
+  p.d = d.d;
+  p.kind = d.kind;
+  p.m = d.m;
+  p.L = d.L;
+  p.N = d.N;
+  for (int k = 0; k < d.N; ++k) {
+    p.dims[k] = d.dims[k];
+    p.mdims[k] = d.mdims[k];
+  }
+  p.dsum = int32_t(f->host.dsum);
+  p.bins = f->d_bins;
+  p.signs = f->d_signs;
+  p.b32 = f->d_b32;
+  p.b64 = f->d_b64;
+  p.ka = f->d_ka;
+  p.kb = f->d_kb;
+  p.w = d.w;
+  p.sqrtm = kind_scaled(d.kind) ? std::sqrt(double(d.m)) : 1.0;
+  if (kind_is_srp(d.kind))
+    p.bits = static_cast<uint64_t *>(codes);
+  else
+    p.codes = static_cast<int32_t *>(codes);
+  p.keys = keys;
+  p.key_ld = key_ld;
+  p.proj = proj;
+  p.counters = counters;
+  p.status = f->d_status;
+  SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, X->dtype);
+  if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
+  LSH_CUDA_TRY(launch_sketch_dense(p, stream));
+  count_launches(1);
+  return LSH_OK;
+}
+
+lsh_family_desc normalized(const lsh_family_desc &in) {
+  lsh_family_desc d = in;
+  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP || kind_is_dense(d.kind)) && d.N == 0) {
+    d.N = 1;
+    d.dims[0] = d.d;
+    d.mdims[0] = d.m;
+  }
+  return d;
+}
+
+// The per-call temporaries (keys, sort buffers, counters) come from the
+// device's default stream-ordered pool.  Keep freed blocks in the pool instead
+// of returning them to the driver at every synchronisation, so that repeated
+// calls reuse them without remapping (done once per device).
+void keep_pool_warm() {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
+  const uint64_t bit = uint64_t(1) << dev;
+  if (done_mask.load() & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done_mask.fetch_or(bit);
+}
+
+// Hash X into temporary keys and sort/segment them into the index's arrays.
+lsh_status index_fill(lsh_index_s *idx, const lsh_matrix *X, cudaStream_t stream) {
+  const int L = idx->L;
+  const int64_t n = idx->n;
+  keep_pool_warm();
+  uint64_t *keys = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&keys), sizeof(uint64_t) * size_t(n) * L, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync keys");
+  lsh_status st = hash_impl(idx->fam, X, nullptr, keys, n, nullptr, nullptr, stream);
+  if (st == LSH_OK) {
+    e = build_tables(keys, n, L, idx->d_ids, idx->d_ukeys, idx->d_offsets, idx->d_nb, stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "build_tables");
+  }
+  cudaFreeAsync(keys, stream);
+  return st;
+}
+
+}  // namespace
+}  // namespace lsh
+
+using namespace lsh;
+
+extern "C" {
+
+const char *lsh_last_error(void) { return g_last_error.c_str(); }
+
+const char *lsh_version(void) { return "lsh-gb300 0.1 (sm_103a)"; }
+
+uint64_t lsh_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
+  if (!desc || !out) return fail(LSH_EINVAL, "NULL argument");
+  *out = nullptr;
+  const lsh_family_desc d = normalized(*desc);
+  lsh_status st = validate_desc(d);
+  if (st != LSH_OK) return st;
+  lsh_family_s *f = new (std::nothrow) lsh_family_s();
+  if (!f) return fail(LSH_ENOMEM, "host allocation");
+  try {
+    sample_family(d, f->host);
+  } catch (const std::bad_alloc &) {
+    delete f;
+    return fail(LSH_ENOMEM, "host allocation");
+  }
+  cudaGetDevice(&f->device);
+  const HostFamily &h = f->host;
+  cudaError_t e = cudaSuccess;
+  if (!h.bins.empty()) {
+    std::vector<uint16_t> b16(h.bins.begin(), h.bins.end());
+    e = upload(&f->d_bins, b16.data(), b16.size());
+    if (e == cudaSuccess) e = upload(&f->d_signs, h.signs.data(), h.signs.size());
+  }
+  std::vector<float> b32(h.b.size());
+  for (size_t i = 0; i < b32.size(); ++i) b32[i] = float(h.b[i]);
+  if (e == cudaSuccess) e = upload(&f->d_b32, b32.data(), b32.size());
+  if (e == cudaSuccess) e = upload(&f->d_b64, h.b.data(), h.b.size());
+  if (e == cudaSuccess) e = upload(&f->d_ka, h.ka.data(), h.ka.size());
+  if (e == cudaSuccess) e = upload(&f->d_kb, h.kb.data(), h.kb.size());
+  if (e == cudaSuccess && !h.G.empty()) e = upload(&f->d_G, h.G.data(), h.G.size());
+  if (e == cudaSuccess) e = cudaMalloc(&f->d_status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(f->d_status, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    free_family(f);
+    return cuda_fail(e, "lsh_make_family upload");
+  }
+  *out = f;
+  return LSH_OK;
+}
+
+lsh_status lsh_sample_family_tables(const lsh_family_desc *desc, int32_t *bins, int8_t *signs, float *G,
+                                    double *b, uint32_t *ka, uint32_t *kb) {
+  if (!desc) return fail(LSH_EINVAL, "NULL argument");
+  const lsh_family_desc d = normalized(*desc);
+  lsh_status st = validate_desc(d);
+  if (st != LSH_OK) return st;
+  HostFamily h;
+  try {
+    sample_family(d, h);
+  } catch (const std::bad_alloc &) {
+    return fail(LSH_ENOMEM, "host allocation");
+  }
+  if (bins && !h.bins.empty()) std::memcpy(bins, h.bins.data(), h.bins.size() * sizeof(int32_t));
+  if (signs && !h.signs.empty()) std::memcpy(signs, h.signs.data(), h.signs.size());
+  if (G && !h.G.empty()) std::memcpy(G, h.G.data(), h.G.size() * sizeof(float));
+  if (b) std::memcpy(b, h.b.data(), h.b.size() * sizeof(double));
+  if (ka) std::memcpy(ka, h.ka.data(), h.ka.size() * sizeof(uint32_t));
+  if (kb) std::memcpy(kb, h.kb.data(), h.kb.size() * sizeof(uint32_t));
+  return LSH_OK;
+}
+
+lsh_status lsh_family_describe(lsh_family_t fam, lsh_family_desc *desc) {
+  if (!fam || !desc) return fail(LSH_EINVAL, "NULL argument");
+  *desc = fam->host.desc;
+  return LSH_OK;
+}
+
+lsh_status lsh_family_export(lsh_family_t fam, int32_t *bins, int8_t *signs, float *G, double *b, uint32_t *ka,
+                             uint32_t *kb) {
+  if (!fam) return fail(LSH_EINVAL, "NULL family");
+  const HostFamily &h = fam->host;
+  if (bins && !h.bins.empty()) std::memcpy(bins, h.bins.data(), h.bins.size() * sizeof(int32_t));
+  if (signs && !h.signs.empty()) std::memcpy(signs, h.signs.data(), h.signs.size());
+  if (G && !h.G.empty()) std::memcpy(G, h.G.data(), h.G.size() * sizeof(float));
+  if (b) std::memcpy(b, h.b.data(), h.b.size() * sizeof(double));
+  if (ka) std::memcpy(ka, h.ka.data(), h.ka.size() * sizeof(uint32_t));
+  if (kb) std::memcpy(kb, h.kb.data(), h.kb.size() * sizeof(uint32_t));
+  return LSH_OK;
+}
+
+lsh_status lsh_family_status(lsh_family_t fam, int32_t *status, int32_t clear) {
+  if (!fam || !status) return fail(LSH_EINVAL, "NULL argument");
+  LSH_CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t s = 0;
+  LSH_CUDA_TRY(cudaMemcpy(&s, fam->d_status, sizeof(s), cudaMemcpyDeviceToHost));
+  if (clear) LSH_CUDA_TRY(cudaMemset(fam->d_status, 0, sizeof(uint32_t)));
+  *status = int32_t(s);
+  return LSH_OK;
+}
+
+void lsh_family_destroy(lsh_family_t fam) { free_family(fam); }
+
+lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys, float *proj,
+                    lsh_hash_stats *stats, void *stream_) {
+  if (!fam) return fail(LSH_EINVAL, "NULL family");
+  lsh_status st = validate_matrix(fam, X, true);
+  if (st != LSH_OK) return st;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const lsh_family_desc &d = fam->host.desc;
+  unsigned long long *cnt = nullptr;
+  keep_pool_warm();
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    LSH_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&cnt), CNT_NUM * 8, stream));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, CNT_NUM * 8, stream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(cnt, stream);
+      return cuda_fail(e, "cudaMemsetAsync");
+    }
+  }
+  st = hash_impl(fam, X, codes, keys, X->n, proj, cnt, stream);
+  if (stats) {
+    unsigned long long h[CNT_NUM] = {};
+    cudaError_t e = cudaSuccess;
+    if (st == LSH_OK) e = cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(cnt, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (st != LSH_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "lsh_hash stats");
+    stats->n_entries = X->n * int64_t(d.L) * d.m;
+    stats->n_flagged = int64_t(h[CNT_FLAGGED]);
+    stats->n_changed = int64_t(h[CNT_CHANGED]);
+    stats->n_nonfinite = int64_t(h[CNT_NONFINITE]);
+    stats->n_overflow = int64_t(h[CNT_OVERFLOW]);
+    if (stats->n_nonfinite) return fail(LSH_ENONFINITE, "input rows hold NaN or Inf");
+    if (stats->n_overflow) return fail(LSH_ERANGE, "E2LSH code outside int32");
+  }
+  return st;
+}
+
+lsh_status lsh_build_index(lsh_family_t fam, const lsh_matrix *X, int32_t keep_data, lsh_index_t *out,
+                           void *stream_) {
+  if (!fam || !out) return fail(LSH_EINVAL, "NULL argument");
+  *out = nullptr;
+  lsh_status st = validate_matrix(fam, X, true);
+  if (st != LSH_OK) return st;
+  if (keep_data && X->rowptr) return fail(LSH_EUNSUPPORTED, "keep_data needs dense rows");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int L = fam->host.desc.L;
+  const int64_t n = X->n;
+  lsh_index_s *idx = new (std::nothrow) lsh_index_s();
+  if (!idx) return fail(LSH_ENOMEM, "host allocation");
+  idx->fam = fam;
+  idx->n = n;
+  idx->L = L;
+  idx->d = X->d;
+  auto cleanup = [&](lsh_status s) {
+    lsh_index_destroy(idx);
+    return s;
+  };
+  cudaError_t e = cudaMalloc(&idx->d_nb, sizeof(int64_t) * L);
+  if (e == cudaSuccess && n > 0) e = cudaMalloc(&idx->d_ids, sizeof(uint32_t) * size_t(n) * L);
+  if (e == cudaSuccess && n > 0) e = cudaMalloc(&idx->d_ukeys, sizeof(uint64_t) * size_t(n) * L);
+  if (e == cudaSuccess) e = cudaMalloc(&idx->d_offsets, sizeof(uint32_t) * size_t(n + 1) * L);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "lsh_build_index allocation"));
+  if (keep_data && n > 0) {
+    const size_t es = dtype_size(X->dtype);
+    e = cudaMalloc(&idx->d_data, es * size_t(n) * X->d);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(idx->d_data, es * X->d, X->values, es * X->ld, es * X->d, size_t(n),
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "lsh_build_index data copy"));
+    idx->data_dtype = X->dtype;
+    idx->data_ld = X->d;
+  }
+  if (n == 0) {
+    e = cudaMemsetAsync(idx->d_nb, 0, sizeof(int64_t) * L, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(idx->d_offsets, 0, sizeof(uint32_t) * L, stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
+    *out = idx;
+    return LSH_OK;
+  }
+  st = index_fill(idx, X, stream);
+  if (st != LSH_OK) return cleanup(st);
+  *out = idx;
+  return LSH_OK;
+}
+
+lsh_status lsh_index_rebuild(lsh_index_t idx, const lsh_matrix *X, void *stream_) {
+  if (!idx) return fail(LSH_EINVAL, "NULL index");
+  lsh_status st = validate_matrix(idx->fam, X, true);
+  if (st != LSH_OK) return st;
+  if (X->n != idx->n) return fail(LSH_EINVAL, "rebuild needs the same n as the index");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (idx->d_data) {
+    if (X->rowptr || X->dtype != idx->data_dtype) return fail(LSH_EINVAL, "rebuild data must match the kept data");
+    const size_t es = dtype_size(X->dtype);
+    if (X->n > 0)
+      LSH_CUDA_TRY(cudaMemcpy2DAsync(idx->d_data, es * X->d, X->values, es * X->ld, es * X->d, size_t(X->n),
+                                     cudaMemcpyDeviceToDevice, stream));
+  }
+  if (X->n == 0) return LSH_OK;
+  return index_fill(idx, X, stream);
+}
+
+lsh_status lsh_index_info(lsh_index_t idx, int64_t *n, int64_t *nbuckets) {
+  if (!idx) return fail(LSH_EINVAL, "NULL index");
+  if (n) *n = idx->n;
+  if (nbuckets) {
+    LSH_CUDA_TRY(cudaDeviceSynchronize());
+    LSH_CUDA_TRY(cudaMemcpy(nbuckets, idx->d_nb, sizeof(int64_t) * idx->L, cudaMemcpyDeviceToHost));
+  }
+  return LSH_OK;
+}
+
+lsh_status lsh_index_export(lsh_index_t idx, uint32_t *ids, uint64_t *ukeys, uint32_t *offsets, int64_t *nb) {
+  if (!idx) return fail(LSH_EINVAL, "NULL index");
+  LSH_CUDA_TRY(cudaDeviceSynchronize());
+  const size_t nL = size_t(idx->n) * idx->L;
+  if (ids && nL) LSH_CUDA_TRY(cudaMemcpy(ids, idx->d_ids, nL * 4, cudaMemcpyDeviceToHost));
+  if (ukeys && nL) LSH_CUDA_TRY(cudaMemcpy(ukeys, idx->d_ukeys, nL * 8, cudaMemcpyDeviceToHost));
+  if (offsets)
+    LSH_CUDA_TRY(cudaMemcpy(offsets, idx->d_offsets, size_t(idx->n + 1) * idx->L * 4, cudaMemcpyDeviceToHost));
+  if (nb) LSH_CUDA_TRY(cudaMemcpy(nb, idx->d_nb, sizeof(int64_t) * idx->L, cudaMemcpyDeviceToHost));
+  return LSH_OK;
+}
+
+lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *ids, float *dist,
+                     lsh_query_stats *stats, void *stream) {
+  if (!idx || !Q) return fail(LSH_EINVAL, "NULL argument");
+  (void)Q;
+  (void)k;
+  (void)ids;
+  (void)dist;
+  (void)stats;
+  (void)stream;
+  return fail(LSH_EUNSUPPORTED, "lsh_query is not in this build yet");
+}
+
+void lsh_index_destroy(lsh_index_t idx) {
+  if (!idx) return;
+  cudaFree(idx->d_ids);
+  cudaFree(idx->d_ukeys);
+  cudaFree(idx->d_offsets);
+  cudaFree(idx->d_nb);
+  cudaFree(idx->d_data);
+  delete idx;
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+"""ctypes binding of the C ABI in include/lsh.h (argument marshalling only).
+
+Every step of the hot path runs in liblsh_gb300.so; this module converts torch
+tensors (device memory, streams) into the plain pointers and sizes the ABI
+takes, and raises on a non-OK status.  It never computes a hash itself and has
+no fallback: if the library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsh_gb300.so")
+
+# Kinds and dtypes: the numbering of lsh_kind / lsh_dtype.
+E2LSH, SRP, CS_E2LSH, HCS_E2LSH, CS_SRP, HCS_SRP = range(6)
+KINDS = {"e2lsh": E2LSH, "srp": SRP, "cs_e2lsh": CS_E2LSH, "hcs_e2lsh": HCS_E2LSH,
+         "cs_srp": CS_SRP, "hcs_srp": HCS_SRP}
+F32, BF16, F16, FP8_E4M3 = range(4)
+_TORCH_DTYPE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.uint8: FP8_E4M3,
+                torch.float8_e4m3fn: FP8_E4M3}
+STATUS = {0: "LSH_OK", 1: "LSH_EINVAL", 2: "LSH_ENOMEM", 3: "LSH_ECUDA", 4: "LSH_ETIMEOUT",
+          5: "LSH_ENONFINITE", 6: "LSH_EUNSUPPORTED", 7: "LSH_ERANGE"}
+
+MAX_MODES = 8
+
+
+class LshError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FamilyDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("dims", ctypes.c_int32 * MAX_MODES), ("mdims", ctypes.c_int32 * MAX_MODES),
+                ("w", ctypes.c_double), ("seed", ctypes.c_uint64), ("compute", ctypes.c_int32)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("n", ctypes.c_int64), ("d", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("values", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("row_scale", ctypes.c_void_p)]
+
+
+class HashStats(ctypes.Structure):
+    _fields_ = [("n_entries", ctypes.c_int64), ("n_flagged", ctypes.c_int64),
+                ("n_changed", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
+                ("n_overflow", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_unique", ctypes.c_int64), ("max_unique", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol of include/lsh.h
+P = ctypes.c_void_p
+SIGNATURES = [
+    ("lsh_last_error", ctypes.c_char_p, []),
+    ("lsh_version", ctypes.c_char_p, []),
+    ("lsh_launch_count", ctypes.c_uint64, []),
+    ("lsh_make_family", ctypes.c_int, [ctypes.POINTER(FamilyDesc), ctypes.POINTER(P)]),
+    ("lsh_sample_family_tables", ctypes.c_int, [ctypes.POINTER(FamilyDesc), P, P, P, P, P, P]),
+    ("lsh_family_describe", ctypes.c_int, [P, ctypes.POINTER(FamilyDesc)]),
+    ("lsh_family_export", ctypes.c_int, [P, P, P, P, P, P, P]),
+    ("lsh_family_status", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    ("lsh_family_destroy", None, [P]),
+    ("lsh_hash", ctypes.c_int, [P, ctypes.POINTER(Matrix), P, P, P, ctypes.POINTER(HashStats), P]),
+    ("lsh_build_index", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, ctypes.POINTER(P), P]),
+    ("lsh_index_rebuild", ctypes.c_int, [P, ctypes.POINTER(Matrix), P]),
+    ("lsh_index_info", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), P]),
+    ("lsh_index_export", ctypes.c_int, [P, P, P, P, P]),
+    ("lsh_query", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, P, P,
+                                 ctypes.POINTER(QueryStats), P]),
+    ("lsh_index_destroy", None, [P]),
+]
+
+
+def lib():
+    """Load liblsh_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2503_06737_gb300.build` (there is no fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def launch_count() -> int:
+    return int(lib().lsh_launch_count())
+
+
+def _check(st: int):
+    if st != 0:
+        raise LshError(st, lib().lsh_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dense_matrix(X: torch.Tensor, row_scale: torch.Tensor | None = None) -> Matrix:
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D tensor with unit column stride")
+    if X.dtype not in _TORCH_DTYPE:
+        raise ValueError(f"unsupported dtype {X.dtype}")
+    mtx = Matrix()
+    mtx.dtype = _TORCH_DTYPE[X.dtype]
+    mtx.n, mtx.d = X.shape
+    mtx.ld = X.stride(0) if X.shape[0] > 1 else X.shape[1]
+    mtx.values = X.data_ptr() if X.numel() else None
+    mtx.row_scale = None if row_scale is None else row_scale.data_ptr()
+    return mtx
+
+
+def csr_matrix(rowptr: torch.Tensor, col: torch.Tensor, values: torch.Tensor, d: int) -> Matrix:
+    mtx = Matrix()
+    mtx.dtype = F32
+    mtx.n = rowptr.shape[0] - 1
+    mtx.d = d
+    mtx.ld = d
+    mtx.values = values.data_ptr() if values.numel() else None
+    mtx.col = col.data_ptr() if col.numel() else None
+    mtx.rowptr = rowptr.data_ptr()
+    return mtx
+
+
+def make_desc(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32) -> FamilyDesc:
+    desc = FamilyDesc()
+    desc.kind = KINDS.get(kind, kind)
+    desc.d, desc.m, desc.L = d, m, L
+    if dims is None:
+        dims, mdims = [d], [m]
+    desc.N = len(dims)
+    for k, (a, b) in enumerate(zip(dims, mdims)):
+        desc.dims[k] = a
+        desc.mdims[k] = b
+    desc.w = float(w)
+    desc.seed = int(seed)
+    desc.compute = compute
+    return desc
+
+
+def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None):
+    """The library's host sampler alone (no device): dict of numpy tables."""
+    import numpy as np
+    desc = make_desc(kind, d, m, L, w, seed, dims, mdims)
+    dense = desc.kind in (E2LSH, SRP)
+    dsum = 0 if dense else sum(desc.dims[k] for k in range(desc.N))
+    bins = np.empty((L, dsum), np.int32)
+    signs = np.empty((L, dsum), np.int8)
+    G = np.empty((d, m * L), np.float32) if dense else None
+    b = np.empty((L, m), np.float64)
+    ka = np.empty((L, m), np.uint32)
+    kb = np.empty((L, m), np.uint32)
+    p = lambda a: None if a is None or a.size == 0 else ctypes.c_void_p(a.ctypes.data)
+    _check(lib().lsh_sample_family_tables(ctypes.byref(desc), p(bins), p(signs), p(G), p(b), p(ka), p(kb)))
+    return dict(bins=bins, signs=signs, G=G, b=b, ka=ka, kb=kb)
+
+
+class Family:
+    """An LSH family drawn on the host and resident on the current device."""
+
+    def __init__(self, kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32):
+        desc = FamilyDesc()
+        desc.kind = KINDS.get(kind, kind)
+        desc.d, desc.m, desc.L = d, m, L
+        if dims is None:
+            dims, mdims = [d], [m]
+        desc.N = len(dims)
+        for k, (a, b) in enumerate(zip(dims, mdims)):
+            desc.dims[k] = a
+            desc.mdims[k] = b
+        desc.w = float(w)
+        desc.seed = int(seed)
+        desc.compute = compute
+        h = ctypes.c_void_p()
+        _check(lib().lsh_make_family(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+        self.kind, self.d, self.m, self.L, self.w, self.seed = desc.kind, d, m, L, float(w), seed
+        self.dims, self.mdims = list(dims), list(mdims)
+
+    @property
+    def is_srp(self):
+        return self.kind in (SRP, CS_SRP, HCS_SRP)
+
+    def export(self):
+        """Host copies of the drawn tables (for parity checks)."""
+        import numpy as np
+        dsum = sum(self.dims) if self.kind not in (E2LSH, SRP) else 0
+        bins = np.empty((self.L, dsum), np.int32)
+        signs = np.empty((self.L, dsum), np.int8)
+        G = np.empty((self.d, self.m * self.L), np.float32) if self.kind in (E2LSH, SRP) else None
+        b = np.empty((self.L, self.m), np.float64)
+        ka = np.empty((self.L, self.m), np.uint32)
+        kb = np.empty((self.L, self.m), np.uint32)
+        p = lambda a: None if a is None or a.size == 0 else ctypes.c_void_p(a.ctypes.data)
+        _check(lib().lsh_family_export(self.handle, p(bins), p(signs), p(G), p(b), p(ka), p(kb)))
+        return dict(bins=bins, signs=signs, G=G, b=b, ka=ka, kb=kb)
+
+    def status(self, clear=True) -> int:
+        s = ctypes.c_int32()
+        _check(lib().lsh_family_status(self.handle, ctypes.byref(s), int(clear)))
+        return int(s.value)
+
+    def code_shape(self, n):
+        if self.is_srp:
+            return (n, self.L, (self.m + 63) // 64), torch.int64
+        return (n, self.L, self.m), torch.int32
+
+    def hash(self, X=None, *, csr=None, codes=False, keys=True, proj=False, stats=False,
+             row_scale=None, stream=None):
+        """Hash a dense tensor X [n, d] (or csr=(rowptr, col, values)) on its device.
+        Returns a dict with the requested outputs ('codes', 'keys', 'proj', 'stats')."""
+        mtx = dense_matrix(X, row_scale) if csr is None else csr_matrix(*csr, d=self.d)
+        n = int(mtx.n)
+        dev = X.device if X is not None else csr[0].device
+        out = {}
+        if codes:
+            shp, dt = self.code_shape(n)
+            out["codes"] = torch.empty(shp, dtype=dt, device=dev)
+        if keys:
+            out["keys"] = torch.empty((self.L, n), dtype=torch.int64, device=dev)
+        if proj:
+            out["proj"] = torch.empty((n, self.L, self.m), dtype=torch.float32, device=dev)
+        st = HashStats() if stats else None
+        _check(lib().lsh_hash(self.handle, ctypes.byref(mtx), _ptr(out.get("codes")),
+                              _ptr(out.get("keys")), _ptr(out.get("proj")),
+                              ctypes.byref(st) if st is not None else None, _stream(stream)))
+        if st is not None:
+            out["stats"] = st.as_dict()
+        return out
+
+    def hash_into(self, mtx: Matrix, codes_ptr, keys_ptr, proj_ptr, stream=None, stats=None):
+        """Raw-pointer form (the bench's end-to-end leg)."""
+        _check(lib().lsh_hash(self.handle, ctypes.byref(mtx), codes_ptr, keys_ptr, proj_ptr,
+                              ctypes.byref(stats) if stats is not None else None, _stream(stream)))
+
+    def build_index(self, X=None, *, csr=None, keep_data=True, stream=None) -> "Index":
+        mtx = dense_matrix(X) if csr is None else csr_matrix(*csr, d=self.d)
+        h = ctypes.c_void_p()
+        _check(lib().lsh_build_index(self.handle, ctypes.byref(mtx), int(bool(keep_data)),
+                                     ctypes.byref(h), _stream(stream)))
+        return Index(self, h)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().lsh_family_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Index:
+    """The L hash tables over a batch of points (owns device memory)."""
+
+    def __init__(self, family: Family, handle):
+        self.family = family
+        self.handle = handle
+
+    def rebuild(self, X, stream=None):
+        mtx = dense_matrix(X)
+        _check(lib().lsh_index_rebuild(self.handle, ctypes.byref(mtx), _stream(stream)))
+
+    def rebuild_into(self, mtx: Matrix, stream=None):
+        _check(lib().lsh_index_rebuild(self.handle, ctypes.byref(mtx), _stream(stream)))
+
+    def info(self):
+        import numpy as np
+        n = ctypes.c_int64()
+        nb = np.empty(self.family.L, np.int64)
+        _check(lib().lsh_index_info(self.handle, ctypes.byref(n), ctypes.c_void_p(nb.ctypes.data)))
+        return int(n.value), nb
+
+    def export(self):
+        import numpy as np
+        n, _ = self.info()
+        L = self.family.L
+        ids = np.empty((L, n), np.uint32)
+        ukeys = np.empty((L, max(n, 1)), np.uint64)
+        offsets = np.empty((L, n + 1), np.uint32)
+        nb = np.empty(L, np.int64)
+        p = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(lib().lsh_index_export(self.handle, p(ids) if n else None, p(ukeys) if n else None,
+                                      p(offsets), p(nb)))
+        return dict(ids=ids, ukeys=ukeys, offsets=offsets, nb=nb)
+
+    def query(self, Q, k=10, stats=False, stream=None):
+        mtx = dense_matrix(Q)
+        q = int(mtx.n)
+        ids = torch.empty((q, k), dtype=torch.int32, device=Q.device)
+        dist = torch.empty((q, k), dtype=torch.float32, device=Q.device)
+        st = QueryStats() if stats else None
+        _check(lib().lsh_query(self.handle, ctypes.byref(mtx), int(k), _ptr(ids), _ptr(dist),
+                               ctypes.byref(st) if st is not None else None, _stream(stream)))
+        out = {"ids": ids, "dist": dist}
+        if st is not None:
+            out["stats"] = st.as_dict()
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().lsh_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

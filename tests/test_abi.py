@@ -1,0 +1,90 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/lsh.h declares, its host-side family sampler draws exactly the
+tables the oracle draws from the same seed, and invalid descriptions are
+rejected on the host."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lsh.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2503_06737_gb300 import build, lsh
+    build.build()
+    return lsh
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    lib = L.lib()
+    names = declared_functions()
+    assert len(names) >= 14
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    bound = {s[0] for s in L.SIGNATURES}
+    assert set(names) == bound, set(names) ^ bound
+
+
+def test_version(L):
+    assert b"sm_103a" in L.lib().lsh_version()
+
+
+@pytest.mark.parametrize("kind,d,m,Lt,dims,mdims,seed", [
+    ("cs_e2lsh", 128, 16, 10, None, None, 42),
+    ("cs_srp", 20000, 256, 3, None, None, 43),
+    ("hcs_e2lsh", 960, 64, 50, [8, 10, 12], [4, 4, 4], 44),
+    ("hcs_srp", 20000, 256, 4, [100, 200], [16, 16], 45),
+    ("hcs_e2lsh", 90, 16, 2, [8, 12], [4, 4], 46),
+    ("e2lsh", 128, 16, 4, None, None, 47),
+    ("srp", 64, 8, 3, None, None, 48),
+])
+def test_sampler_matches_oracle(L, orc, kind, d, m, Lt, dims, mdims, seed):
+    a = L.sample_family_tables(kind, d, m, Lt, w=4.0, seed=seed, dims=dims, mdims=mdims)
+    f = orc.family(kind, d, m, Lt, w=4.0, seed=seed, dims=dims, mdims=mdims)
+    assert np.array_equal(a["b"], f.b)
+    assert np.array_equal(a["ka"], f.ka) and np.array_equal(a["kb"], f.kb)
+    if f.bins is not None:
+        assert np.array_equal(a["bins"], f.bins) and np.array_equal(a["signs"], f.signs)
+    if f.G is not None:
+        assert np.array_equal(a["G"], f.G)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(kind="cs_e2lsh", d=0, m=4, L=1),
+    dict(kind="cs_e2lsh", d=8, m=0, L=1),
+    dict(kind="cs_e2lsh", d=8, m=4, L=0),
+    dict(kind="cs_e2lsh", d=8, m=4, L=1, w=0.0),
+    dict(kind="cs_e2lsh", d=8, m=4, L=1, w=float("nan")),
+    dict(kind="hcs_e2lsh", d=100, m=16, L=1, dims=[8, 12], mdims=[4, 4]),   # 96 < 100
+    dict(kind="hcs_e2lsh", d=96, m=16, L=1, dims=[8, 12], mdims=[4, 5]),    # 20 != 16
+    dict(kind="cs_srp", d=96, m=16, L=1, dims=[8, 12], mdims=[4, 4]),       # CS takes N = 1
+    dict(kind=9, d=8, m=4, L=1),
+])
+def test_invalid_descriptions(L, bad):
+    with pytest.raises(L.LshError) as e:
+        L.sample_family_tables(**bad)
+    assert e.value.status == 1  # LSH_EINVAL
+    assert L.lib().lsh_last_error()
+
+
+def test_null_arguments(L):
+    import ctypes
+    lib = L.lib()
+    assert lib.lsh_make_family(None, None) == 1
+    assert lib.lsh_hash(None, None, None, None, None, None, None) == 1
+    assert lib.lsh_build_index(None, None, 0, None, None) == 1
+    assert lib.lsh_query(None, None, 10, None, None, None, None) == 1
+    assert lib.lsh_family_export(None, None, None, None, None, None, None) == 1
+    assert lib.lsh_index_export(None, None, None, None, None) == 1
+    lib.lsh_family_destroy(None)
+    lib.lsh_index_destroy(None)
