@@ -3,6 +3,7 @@
 // key multipliers), drawn from a 64-bit seed with SplitMix64 (Steele, Lea &
 // Flood, OOPSLA 2014).  Compiled with -ffp-contract=off so the Box-Muller
 // arithmetic is one IEEE rounding per operation.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -90,6 +91,34 @@ void sample_family(const lsh_family_desc &d, HostFamily &hf) {
     }
     draw_offsets_and_keys(s, d, t, hf);
   }
+}
+
+int sketch_capacity(const HostFamily &hf) {
+  const lsh_family_desc &d = hf.desc;
+  if (kind_is_dense(d.kind)) return 0;
+  int best = 0;
+  std::vector<uint32_t> cnt(size_t(2) * d.m);
+  for (int t = 0; t < d.L; ++t) {
+    std::fill(cnt.begin(), cnt.end(), 0u);
+    const int32_t *hb = hf.bins.data() + size_t(t) * hf.dsum;
+    const int8_t *sb = hf.signs.data() + size_t(t) * hf.dsum;
+    for (int j = 0; j < d.d; ++j) {
+      int r = j, off = 0, stride = 1, bin = 0, neg = 0;
+      for (int k = 0; k < d.N; ++k) {
+        const int ik = r % d.dims[k];
+        r /= d.dims[k];
+        bin += hb[off + ik] * stride;
+        neg ^= sb[off + ik] < 0 ? 1 : 0;
+        stride *= d.mdims[k];
+        off += d.dims[k];
+      }
+      ++cnt[size_t(2) * bin + neg];
+    }
+    int total = 0;
+    for (uint32_t c : cnt) total += int((c + 3) & ~3u);
+    best = std::max(best, total);
+  }
+  return best;
 }
 
 }  // namespace lsh

@@ -3,29 +3,39 @@
 //
 // Design (sm_103a):
 //   * A CTA owns a group of Lg tables and walks row tiles of 32*RG rows.  Its
-//     tables are staged once in shared memory as per-table member lists: the
-//     coordinates j < d sorted by (bin, j), each entry the byte offset 4j with
-//     the sign of s(j) (count sketch) or of prod_k s_k(i_k) (HCS) in bit 31,
-//     plus the bin start offsets.  The HCS lists are derived in the CTA from
-//     the per-mode tables h_k, s_k (O(N d^(1/N)) words per table in HBM).
+//     tables are staged once in shared memory as per-table member lists: for
+//     each bin, the coordinates j < d with s = +1 (ascending j), then those
+//     with s = -1, each half padded to a multiple of four with the offset of
+//     the row's zero slot, every entry the byte offset 4j.  HCS lists are
+//     derived in the CTA from the per-mode tables h_k, s_k (the sign of j is
+//     prod_k s_k(i_k)), so HBM holds only O(N d^(1/N)) words per table.
 //   * The row tile is read once from HBM with coalesced loads into a padded
-//     row-major tile (row stride d+1 words, so lane r reading row r hits bank
-//     (r + j) mod 32: conflict free).  The CTAs of the G table groups that
-//     share a tile run concurrently, so the tile is fetched from HBM once and
-//     from L2 for the other groups.
-//   * Lane = row, warp = (row group, table).  Every member-list read is a
-//     warp-uniform broadcast; every x read is one conflict-free LDS.32; the
-//     bin sum lives in one register and is discretised, margin-checked and
-//     folded into the key as soon as the bin ends.  No atomics, no partial
-//     bins in memory.
-//   * Exactness: the FP32 sum of the k terms of a bin is within
-//     E = gamma_{k-1} k max|x| of the exact sum (Higham's bound for any
-//     summation order); the FP64 oracle is within gamma64_{k-1} k max|x| of
-//     it.  The discretisation adds a few rounding errors, bounded relative to
-//     |t|.  An entry whose FP32 value lies within that total bound of an
-//     integer (E2LSH) or of 0 (SRP) is recomputed by its lane in FP64 from
-//     the same staged tile, in ascending j, with one IEEE rounding per
-//     operation -- the canonical value of Definitions 12/19/25/31.
+//     row-major tile (row stride d+1 words: lane r reading row r hits bank
+//     (r + j) mod 32, conflict free; word d is the zero slot).  The next tile
+//     is prefetched into L2 while this one is hashed; the CTAs of the G table
+//     groups that share a tile run concurrently, so it leaves HBM once.
+//   * Lane = row.  A table is split over WPT warps (bins l = k, k+WPT, ...),
+//     which gives the SM enough independent shared-memory loads in flight.
+//     Entries are read four at a time as warp-uniform 128-bit broadcasts; each
+//     x read is one conflict-free 32-bit load into one of four accumulators.
+//     Partial keys of the warps of one table are combined in shared memory:
+//     the key fold is a sum mod 2^32 (E2LSH, SRP m > 64) or an OR of bits
+//     (SRP m <= 64), so partials combine exactly.
+//   * Exactness.  The FP32 sum of the k terms of a bin differs from the exact
+//     sum by at most gamma_{k-1} * sum|x_j| <= gamma_{k-1} * k * max|x|
+//     (Higham's bound, any summation order; zero padding adds no error), and
+//     the FP64 reference by at most gamma64_{k-1} * k * max|x| (covered by a
+//     2% widening).  For E2LSH, with y = the FP32 sum, t = fl(fl(fma(sqrt(m),
+//     y, b)) * fl(1/w)):
+//        |t - t_fp64| <= (sqrt(m)/w) E + 4.1u (sqrt(m)|y| + b)/w + 2.1u(|t|+1)
+//                     <= A max|x| + 10.2u |t| + 15.3u,
+//     using (sqrt(m)|y| + b)/w <= 1.0001 |t| + 2 (b < w), where u = 2^-24,
+//     A = 1.02 (sqrt(m)/w) gamma_{k-1}(1 + 2 gamma) k, and the last term also
+//     covers the rounding of fr = t - floor(t) and 1 - fr.  An entry whose t
+//     lies within that bound of an integer (E2LSH), or whose |y| is within
+//     A max|x| of 0 (SRP, A without sqrt(m)/w), is recomputed by its lane in
+//     FP64 from the same staged tile, in ascending j, one IEEE rounding per
+//     operation: the canonical value of Definitions 12/19/25/31.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,8 +50,9 @@ constexpr float kU32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of FP32
 constexpr int kMaxSmem = 232448;                 // 227 KB opt-in per block
 
 struct Plan {
-  int Lg, G, RG, W, smem;
-  int off_ent, off_boff, off_b, off_x, off_xmax, off_bad;
+  int Lg, G, RG, WPT, W, smem;
+  int cap;       // entry capacity per table (multiple of 4)
+  int off_ent, off_seg, off_cst, off_key, off_x, off_xmax, off_bad;
   int x_stride;  // d + 1 words
 };
 
@@ -53,10 +64,11 @@ struct Args {
   float sqrtm_f, invw_f;
 };
 
-__device__ __forceinline__ float load_x(const void *X, int dtype, int64_t idx) {
-  if (dtype == LSH_F32) return __ldg(reinterpret_cast<const float *>(X) + idx);
+template <int DT>
+__device__ __forceinline__ float load_x(const void *X, int64_t idx) {
+  if (DT == LSH_F32) return __ldg(reinterpret_cast<const float *>(X) + idx);
   const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(X) + idx);
-  if (dtype == LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
+  if (DT == LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
   return __half2float(__ushort_as_half(h));
 }
 
@@ -82,38 +94,54 @@ __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, i
   }
 }
 
-// Build the member list of table t into ent[0..d) and boff[0..m] (one warp).
-__device__ void build_members(const SketchLaunch &p, int t, uint32_t *ent, uint16_t *boff,
-                              uint32_t *cnt, int lane) {
+// Stage table t (one warp): member list (sign-split, quad-padded) and the
+// per-bin records seg[l] = {start, quads(+) | quads(-) << 16},
+// cst[l] = {b_l (f32 bits), A_l, ka_l, kb_l}.
+__device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_t *ent, uint2 *seg,
+                            uint4 *cst, uint32_t *scratch, int lane) {
   const int d = p.d, m = p.m;
-  for (int l = lane; l < m; l += kWarp) cnt[l] = 0;
+  uint32_t *cur = scratch;  // [2m]: counts, then write cursors (key = 2 bin + neg)
+  for (int i = lane; i < 2 * m; i += kWarp) cur[i] = 0;
   __syncwarp();
   for (int j = lane; j < d; j += kWarp) {
     int bin;
     uint32_t neg;
     coord_bin(p, t, j, bin, neg);
-    atomicAdd(&cnt[bin], 1u);
+    atomicAdd(&cur[2 * bin + neg], 1u);
   }
   __syncwarp();
-  // exclusive scan of cnt -> boff, cnt becomes the write cursor
+  const uint32_t zslot = uint32_t(d) << 2;
   uint32_t carry = 0;
   for (int base = 0; base < m; base += kWarp) {
     const int l = base + lane;
-    const uint32_t v = l < m ? cnt[l] : 0u;
-    uint32_t s = v;
+    uint32_t cp = 0, cn = 0, sz = 0;
+    if (l < m) {
+      cp = cur[2 * l];
+      cn = cur[2 * l + 1];
+      sz = ((cp + 3) & ~3u) + ((cn + 3) & ~3u);
+    }
+    uint32_t s = sz;
 #pragma unroll
     for (int o = 1; o < kWarp; o <<= 1) {
       const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
       if (lane >= o) s += u;
     }
-    const uint32_t excl = carry + s - v;
+    const uint32_t start = carry + s - sz;
     if (l < m) {
-      boff[l] = uint16_t(excl);
-      cnt[l] = excl;
+      const uint32_t qp = (cp + 3) & ~3u, qn = (cn + 3) & ~3u;
+      seg[l] = make_uint2(start, (qp >> 2) | ((qn >> 2) << 16));
+      for (uint32_t i = cp; i < qp; ++i) ent[start + i] = zslot;
+      for (uint32_t i = cn; i < qn; ++i) ent[start + qp + i] = zslot;
+      cur[2 * l] = start;
+      cur[2 * l + 1] = start + qp;
+      const float k = float(cp + cn);
+      const float g = fmaxf(k - 1.f, 0.f) * kU32;
+      const float A = 1.02f * a_scale * g * (1.f + 2.f * g) * k;
+      cst[l] = make_uint4(__float_as_uint(p.b32[int64_t(t) * m + l]), __float_as_uint(A),
+                          p.ka[int64_t(t) * m + l], p.kb[int64_t(t) * m + l]);
     }
     carry += __shfl_sync(0xffffffffu, s, kWarp - 1);
   }
-  if (lane == 0) boff[m] = uint16_t(d);
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
   for (int base = 0; base < d; base += kWarp) {
@@ -124,17 +152,42 @@ __device__ void build_members(const SketchLaunch &p, int t, uint32_t *ent, uint1
       int bin;
       uint32_t neg;
       coord_bin(p, t, j, bin, neg);
-      const uint32_t peers = __match_any_sync(amask, bin);
-      const uint32_t pos = cnt[bin] + __popc(peers & lt);
-      ent[pos] = (uint32_t(j) << 2) | (neg << 31);
+      const uint32_t key = 2u * uint32_t(bin) + neg;
+      const uint32_t peers = __match_any_sync(amask, key);
+      ent[cur[key] + __popc(peers & lt)] = uint32_t(j) << 2;
       __syncwarp(amask);
-      if ((peers & lt) == 0) cnt[bin] += __popc(peers);
+      if ((peers & lt) == 0) cur[key] += __popc(peers);
     }
     __syncwarp();
   }
 }
 
-template <bool SRP>
+__device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off) {
+  return *reinterpret_cast<const float *>(base + off);
+}
+
+// FP64 recheck of one bin for this lane: merge the two ascending halves back
+// into ascending j and sum s(j) x_j with one IEEE rounding per addition.
+__device__ __noinline__ double bin_fp64(const uint32_t *P, int np, const uint32_t *N, int nn,
+                                        const unsigned char *xr, uint32_t zslot) {
+  int ip = 0, in = 0;
+  double y = 0.0;
+  while (true) {
+    const uint32_t a = ip < np ? P[ip] : zslot;
+    const uint32_t b = in < nn ? N[in] : zslot;
+    if (a == zslot && b == zslot) break;
+    if (a < b) {
+      y = __dadd_rn(y, double(lds_f32(xr, a)));
+      ++ip;
+    } else {
+      y = __dadd_rn(y, -double(lds_f32(xr, b)));
+      ++in;
+    }
+  }
+  return y;
+}
+
+template <bool SRP, int DT>
 __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SketchLaunch &p = a.p;
@@ -147,31 +200,34 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
   const int Lg = min(pl.Lg, p.L - t0);
   if (Lg <= 0 || slot >= a.slots) return;
   const int d = p.d, m = p.m;
+  const int cap = pl.cap;
+  const int WPT = pl.WPT;
 
   uint32_t *ent = reinterpret_cast<uint32_t *>(smem + pl.off_ent);
-  uint16_t *boff = reinterpret_cast<uint16_t *>(smem + pl.off_boff);
-  float *bf = reinterpret_cast<float *>(smem + pl.off_b);
+  uint2 *seg = reinterpret_cast<uint2 *>(smem + pl.off_seg);
+  uint4 *cst = reinterpret_cast<uint4 *>(smem + pl.off_cst);
+  uint2 *kacc = reinterpret_cast<uint2 *>(smem + pl.off_key);  // [R][Lg] partial keys
   float *xs = reinterpret_cast<float *>(smem + pl.off_x);
   float *xmax = reinterpret_cast<float *>(smem + pl.off_xmax);
   int *bad = reinterpret_cast<int *>(smem + pl.off_bad);
 
-  // ---- stage this group's tables (once per CTA) ----
+  const float sq_w = a.sqrtm_f * a.invw_f;
   {
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(xs) + warp * m;  // scratch aliases the tile
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(xs) + warp * 2 * m;  // aliases the tile
     for (int tl = warp; tl < Lg; tl += pl.W)
-      build_members(p, t0 + tl, ent + tl * d, boff + tl * (m + 1), cnt, lane);
-    for (int i = threadIdx.x; i < Lg * m; i += blockDim.x) bf[i] = p.b32[int64_t(t0) * m + i];
+      stage_table(p, t0 + tl, SRP ? 1.f : sq_w, ent + tl * cap, seg + tl * m, cst + tl * m, scratch, lane);
   }
   __syncthreads();
 
   const int R = pl.RG * kWarp;
   const int xst = pl.x_stride;
-  const int ntasks = pl.RG * Lg;
-  const float sq_w = a.sqrtm_f * a.invw_f;
+  const int ntasks = pl.RG * Lg * WPT;
+  const uint32_t zslot = uint32_t(d) << 2;
+  constexpr int es = DT == LSH_F32 ? 4 : 2;
 
   for (int tile = slot; tile < a.ntiles; tile += a.slots) {
     const int64_t row0 = int64_t(tile) * R;
-    // ---- load the row tile (warp per row, coalesced) + max|x| and finiteness ----
+    // ---- load the row tile (warp per row, coalesced, 8 loads in flight) ----
     for (int r = warp; r < R; r += pl.W) {
       const int64_t row = row0 + r;
       float *dst = xs + r * xst;
@@ -179,28 +235,26 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       bool fin = true;
       if (row < p.n) {
         const int64_t base = row * p.ld;
-        int j = lane;
-        for (; j + 3 * kWarp < d; j += 4 * kWarp) {
-          const float v0 = load_x(p.X, p.dtype, base + j);
-          const float v1 = load_x(p.X, p.dtype, base + j + kWarp);
-          const float v2 = load_x(p.X, p.dtype, base + j + 2 * kWarp);
-          const float v3 = load_x(p.X, p.dtype, base + j + 3 * kWarp);
-          dst[j] = v0;
-          dst[j + kWarp] = v1;
-          dst[j + 2 * kWarp] = v2;
-          dst[j + 3 * kWarp] = v3;
-          mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))));
-          fin = fin && isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(v3);
-        }
-        for (; j < d; j += kWarp) {
-          const float v = load_x(p.X, p.dtype, base + j);
-          dst[j] = v;
-          mx = fmaxf(mx, fabsf(v));
-          fin = fin && isfinite(v);
+        for (int j0 = lane; j0 < d; j0 += 8 * kWarp) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u * kWarp;
+            v[u] = j < d ? load_x<DT>(p.X, base + j) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u * kWarp;
+            if (j < d) dst[j] = v[u];
+            mx = fmaxf(mx, fabsf(v[u]));
+            fin = fin && isfinite(v[u]);
+          }
         }
       } else {
         for (int j = lane; j < d; j += kWarp) dst[j] = 0.f;
       }
+      if (lane == 0) dst[d] = 0.f;  // the zero slot the padding entries point at
+      for (int tl = lane; tl < Lg; tl += kWarp) kacc[r * Lg + tl] = make_uint2(0u, 0u);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       const bool allfin = __all_sync(0xffffffffu, fin);
@@ -210,91 +264,100 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       }
     }
     __syncthreads();
+    // ---- prefetch the next tile into L2 while this one is hashed ----
+    if (warp == pl.W - 1) {
+      const int64_t nrow0 = int64_t(tile + a.slots) * R;
+      const char *X = reinterpret_cast<const char *>(p.X);
+      for (int r = 0; r < R; ++r) {
+        const int64_t row = nrow0 + r;
+        if (row >= p.n) break;
+        const char *rp = X + row * p.ld * es;
+        for (int off = lane * 128; off < d * es; off += kWarp * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + off));
+      }
+    }
 
-    // ---- one task = (row group, table): lane = row ----
+    // ---- one task = (row group, table, bin subset): lane = row ----
     for (int task = warp; task < ntasks; task += pl.W) {
-      const int rg = task / Lg;
-      const int tl = task - rg * Lg;
+      const int sub = task % WPT;
+      const int rt = task / WPT;
+      const int rg = rt / Lg;
+      const int tl = rt - rg * Lg;
       const int t = t0 + tl;
       const int r = rg * kWarp + lane;
       const int64_t row = row0 + r;
       const bool valid = row < p.n;
       const bool isbad = bad[r] != 0;
       const float xm = xmax[r];
-      const unsigned char *xrow = reinterpret_cast<const unsigned char *>(xs + r * xst);
-      const uint32_t *E = ent + tl * d;
-      const uint16_t *B = boff + tl * (m + 1);
-      const uint32_t *KA = p.ka + int64_t(t) * m;
-      const uint32_t *KB = p.kb + int64_t(t) * m;
+      const unsigned char *xr = reinterpret_cast<const unsigned char *>(xs + r * xst);
+      const uint32_t *E = ent + tl * cap;
+      const uint2 *S = seg + tl * m;
+      const uint4 *C = cst + tl * m;
       uint32_t ha = 0, hb = 0;
       uint64_t word = 0;
       int nflag = 0, nchanged = 0, novf = 0;
-
-      int beg = B[0];
-      for (int l = 0; l < m; ++l) {
-        const int end = B[l + 1];
-        float acc = 0.f;
-#pragma unroll 4
-        for (int i = beg; i < end; ++i) {
-          const uint32_t e = E[i];
-          const float v = *reinterpret_cast<const float *>(xrow + (e & 0x7fffffffu));
-          acc += __uint_as_float(__float_as_uint(v) ^ (e & 0x80000000u));
+      for (int l = sub; l < m; l += WPT) {
+        const uint2 sg = S[l];
+        const int qp = int(sg.y & 0xffffu), qn = int(sg.y >> 16);
+        const uint4 *Q = reinterpret_cast<const uint4 *>(E + sg.x);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < qp; ++q) {
+          const uint4 e = Q[q];
+          p0 += lds_f32(xr, e.x);
+          p1 += lds_f32(xr, e.y);
+          p2 += lds_f32(xr, e.z);
+          p3 += lds_f32(xr, e.w);
         }
-        const int k = end - beg;
-        // FP32 summation bound: gamma_{k-1} * k * max|x| (gamma_n <= n u (1 + 2 n u)),
-        // widened by 2% to cover the FP64 reference's own error and this arithmetic.
-        const float gk = float(k > 1 ? k - 1 : 0) * kU32;
-        const float E_y = 1.02f * gk * (1.f + 2.f * gk) * float(k) * xm;
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+#pragma unroll 1
+        for (int q = qp; q < qp + qn; ++q) {
+          const uint4 e = Q[q];
+          n0 += lds_f32(xr, e.x);
+          n1 += lds_f32(xr, e.y);
+          n2 += lds_f32(xr, e.z);
+          n3 += lds_f32(xr, e.w);
+        }
+        const float y = ((p0 + p1) + (p2 + p3)) - ((n0 + n1) + (n2 + n3));
+        const uint4 c = C[l];
+        const float A = __uint_as_float(c.y);
         if (SRP) {
-          const bool flag = valid && !isbad && k >= 2 && !(fabsf(acc) > E_y);
-          int bit = acc > 0.f ? 1 : 0;
+          const bool flag = valid && !isbad && !(fabsf(y) > A * xm);
+          int bit = y > 0.f ? 1 : 0;
           if (__any_sync(0xffffffffu, flag)) {
             if (flag) {
-              double y = 0.0;
-              for (int i = beg; i < end; ++i) {
-                const uint32_t e = E[i];
-                const double v = double(*reinterpret_cast<const float *>(xrow + (e & 0x7fffffffu)));
-                y = __dadd_rn(y, (e & 0x80000000u) ? -v : v);
-              }
-              const int b64 = y > 0.0 ? 1 : 0;
+              const uint32_t *P = E + sg.x;
+              const double y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
+              const int b64 = y64 > 0.0 ? 1 : 0;
               ++nflag;
               nchanged += b64 != bit;
               bit = b64;
             }
           }
-          if (p.proj && valid) p.proj[(row * p.L + t) * m + l] = acc;
+          if (p.proj && valid) p.proj[(row * p.L + t) * m + l] = y;
           if (m <= 64) {
             word |= uint64_t(bit) << l;
-          } else {
-            word |= uint64_t(bit) << (l & 63);
-            if (bit) {
-              ha += __ldg(KA + l);
-              hb += __ldg(KB + l);
-            }
-            if ((l & 63) == 63 || l == m - 1) {
-              if (p.bits && valid) p.bits[(row * p.L + t) * ((m + 63) >> 6) + (l >> 6)] = word;
-              word = 0;
-            }
+          } else if (bit) {
+            ha += c.z;
+            hb += c.w;
+            if (p.bits && valid)
+              atomicOr(reinterpret_cast<unsigned long long *>(p.bits) + (row * p.L + t) * ((m + 63) >> 6) + (l >> 6),
+                       1ull << (l & 63));
           }
         } else {
-          const float bl = bf[tl * m + l];
-          const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, acc, bl), a.invw_f);
+          const float bl = __uint_as_float(c.x);
+          const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
           const float fl = floorf(tf);
           const float fr = tf - fl;
           const float dist = fminf(fr, 1.f - fr);
-          const float M = 1.02f * (sq_w * E_y +
-                                   5.f * kU32 * ((a.sqrtm_f * fabsf(acc) + bl) * a.invw_f + fabsf(tf) + 1.f));
-          const bool flag = valid && !isbad && (!(dist > M) || !(fabsf(tf) < 4194304.f));
+          const float M = fmaf(A, xm, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
+          const bool flag = valid && !isbad && !(dist > M && fabsf(tf) < 4194304.f);
           int code = int(fl);
           if (__any_sync(0xffffffffu, flag)) {
             if (flag) {
-              double y = 0.0;
-              for (int i = beg; i < end; ++i) {
-                const uint32_t e = E[i];
-                const double v = double(*reinterpret_cast<const float *>(xrow + (e & 0x7fffffffu)));
-                y = __dadd_rn(y, (e & 0x80000000u) ? -v : v);
-              }
-              const double t1 = __dmul_rn(p.sqrtm, y);
+              const uint32_t *P = E + sg.x;
+              const double y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
+              const double t1 = __dmul_rn(p.sqrtm, y64);
               const double t2 = __dadd_rn(t1, p.b64[int64_t(t) * m + l]);
               const double t3 = __ddiv_rn(t2, p.w);
               const double f = floor(t3);
@@ -311,27 +374,24 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
             }
           }
           if (isbad) code = INT32_MIN;
-          ha += uint32_t(code) * __ldg(KA + l);
-          hb += uint32_t(code) * __ldg(KB + l);
+          ha += uint32_t(code) * c.z;
+          hb += uint32_t(code) * c.w;
           if (valid) {
             if (p.codes) p.codes[(row * p.L + t) * m + l] = code;
-            if (p.proj) p.proj[(row * p.L + t) * m + l] = acc;
+            if (p.proj) p.proj[(row * p.L + t) * m + l] = y;
           }
         }
-        beg = end;
       }
-      if (valid) {
-        uint64_t key;
-        if (SRP && m <= 64) {
-          key = word;
-          if (p.bits) p.bits[row * p.L + t] = word;
-        } else {
-          key = (uint64_t(ha) << 32) | uint64_t(hb);
+      // partial key of this warp -> the (row, table) slot
+      if (SRP && m <= 64) {
+        if (word) {
+          atomicOr(&kacc[r * Lg + tl].x, uint32_t(word));
+          atomicOr(&kacc[r * Lg + tl].y, uint32_t(word >> 32));
         }
-        if (isbad) key = ~0ull;
-        if (p.keys) p.keys[int64_t(t) * p.key_ld + row] = key;
+      } else {
+        atomicAdd(&kacc[r * Lg + tl].x, ha);
+        atomicAdd(&kacc[r * Lg + tl].y, hb);
       }
-      // counters (one atomic per warp and counter)
       if (p.counters) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -347,10 +407,29 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       } else if (__any_sync(0xffffffffu, novf != 0) && lane == 0) {
         atomicOr(p.status, STATUS_OVERFLOW);
       }
-      if (tl == 0 && valid && isbad) {  // one report per bad row
-        if (p.counters) atomicAdd(p.counters + CNT_NONFINITE, 1ull);
-        atomicOr(p.status, STATUS_NONFINITE);
+    }
+    __syncthreads();
+    // ---- keys of the tile: consecutive threads write consecutive rows of a table ----
+    for (int i = threadIdx.x; i < Lg * R; i += blockDim.x) {
+      const int tl = i / R, r = i - tl * R;
+      const int64_t row = row0 + r;
+      if (row >= p.n) continue;
+      const uint2 k2 = kacc[r * Lg + tl];
+      uint64_t key;
+      if (SRP && m <= 64) {
+        key = (uint64_t(k2.y) << 32) | k2.x;
+        if (p.bits) p.bits[row * p.L + t0 + tl] = key;
+      } else {
+        key = (uint64_t(k2.x) << 32) | k2.y;
       }
+      if (bad[r]) {
+        key = ~0ull;
+        if (tl == 0) {
+          if (p.counters) atomicAdd(p.counters + CNT_NONFINITE, 1ull);
+          atomicOr(p.status, STATUS_NONFINITE);
+        }
+      }
+      if (p.keys) p.keys[int64_t(t0 + tl) * p.key_ld + row] = key;
     }
     __syncthreads();
   }
@@ -369,57 +448,73 @@ int num_sms() {
 
 int align16(int v) { return (v + 15) & ~15; }
 
-Plan make_plan(int d, int m, int L, int64_t n) {
+Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   Plan best{};
   best.smem = -1;
   const int sms = num_sms();
   for (int RG = 4; RG >= 1; RG >>= 1) {
-    // prefer enough tiles to fill the GPU twice
     const int64_t ntiles = (n + RG * kWarp - 1) / (RG * kWarp);
-    if (RG > 1 && ntiles < 2 * sms) continue;
-    for (int Lg = (L < 32 ? L : 32); Lg >= 1; --Lg) {
-      const int G = (L + Lg - 1) / Lg;
-      const int Lgb = (L + G - 1) / G;  // balanced group size
-      Plan pl{};
-      pl.Lg = Lgb;
-      pl.G = G;
-      pl.RG = RG;
-      const int tasks = RG * Lgb;
-      int W = tasks < 32 ? tasks : 32;
-      if (tasks > 32) {
-        for (int w = 32; w >= 16; --w)
-          if (tasks % w == 0) { W = w; break; }
+    if (RG > 1 && ntiles < 2 * sms) continue;  // keep every SM busy twice over
+    for (int WPT = 2; WPT >= 1; --WPT) {
+      for (int Lg = (L < 32 ? L : 32); Lg >= 1; --Lg) {
+        const int G = (L + Lg - 1) / Lg;
+        const int Lgb = (L + G - 1) / G;  // balanced group size
+        Plan pl{};
+        pl.Lg = Lgb;
+        pl.G = G;
+        pl.RG = RG;
+        pl.WPT = WPT;
+        const int tasks = RG * Lgb * WPT;
+        int W = tasks < 32 ? tasks : 32;
+        if (tasks > 32) {
+          for (int w = 32; w >= 16; --w)
+            if (tasks % w == 0) { W = w; break; }
+        }
+        if (W < 4) W = 4;
+        pl.W = W;
+        pl.x_stride = d + 1;
+        pl.cap = cap;
+        const int R = RG * kWarp;
+        int off = 0;
+        pl.off_ent = off;
+        off = align16(off + Lgb * cap * 4);
+        pl.off_seg = off;
+        off = align16(off + Lgb * m * 8);
+        pl.off_cst = off;
+        off = align16(off + Lgb * m * 16);
+        pl.off_key = off;
+        off = align16(off + R * Lgb * 8);
+        pl.off_x = off;
+        const int xbytes = R * (d + 1) * 4;
+        const int scratch = W * 2 * m * 4;
+        off = align16(off + (xbytes > scratch ? xbytes : scratch));
+        pl.off_xmax = off;
+        off = align16(off + R * 4);
+        pl.off_bad = off;
+        off = align16(off + R * 4);
+        pl.smem = off;
+        if (off <= kMaxSmem) return pl;
       }
-      if (W < 4) W = 4;
-      pl.W = W;
-      pl.x_stride = d + 1;
-      int off = 0;
-      pl.off_ent = off;
-      off = align16(off + Lgb * d * 4);
-      pl.off_boff = off;
-      off = align16(off + Lgb * (m + 1) * 2);
-      pl.off_b = off;
-      off = align16(off + Lgb * m * 4);
-      pl.off_x = off;
-      const int xbytes = RG * kWarp * (d + 1) * 4;
-      const int scratch = W * m * 4;
-      off = align16(off + (xbytes > scratch ? xbytes : scratch));
-      pl.off_xmax = off;
-      off = align16(off + RG * kWarp * 4);
-      pl.off_bad = off;
-      off = align16(off + RG * kWarp * 4);
-      pl.smem = off;
-      if (off <= kMaxSmem) return pl;
     }
   }
   return best;
 }
 
+template <bool SRP, int DT>
+cudaError_t launch_t(const Args &a, cudaStream_t stream) {
+  const dim3 grid((unsigned)(a.slots * a.pl.G)), block((unsigned)(a.pl.W * kWarp));
+  cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<SRP, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       a.pl.smem);
+  if (e != cudaSuccess) return e;
+  sketch_dense_kernel<SRP, DT><<<grid, block, a.pl.smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-SketchPlan plan_sketch_dense(int d, int m, int L, int dtype) {
+SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype) {
   (void)dtype;
-  Plan pl = make_plan(d, m, L, int64_t(1) << 40);
+  Plan pl = make_plan(d, m, L, cap, int64_t(1) << 40);
   SketchPlan sp{};
   sp.ok = pl.smem > 0;
   if (!sp.ok) return sp;
@@ -428,8 +523,7 @@ SketchPlan plan_sketch_dense(int d, int m, int L, int dtype) {
   sp.row_groups = pl.RG;
   sp.warps = pl.W;
   sp.smem = pl.smem;
-  const int per_sm = kMaxSmem / pl.smem;
-  sp.ctas = num_sms() * (per_sm > 0 ? per_sm : 1);
+  sp.ctas = num_sms();
   return sp;
 }
 
@@ -437,36 +531,25 @@ cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {
   if (p.n <= 0) return cudaSuccess;
   Args a{};
   a.p = p;
-  a.pl = make_plan(p.d, p.m, p.L, p.n);
+  a.pl = make_plan(p.d, p.m, p.L, p.cap, p.n);
   if (a.pl.smem <= 0) return cudaErrorInvalidConfiguration;
   const int R = a.pl.RG * kWarp;
   const int64_t ntiles = (p.n + R - 1) / R;
   if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
   a.ntiles = int(ntiles);
-  int per_sm = kMaxSmem / a.pl.smem;
-  if (per_sm > 2) per_sm = 2;
-  if (per_sm < 1) per_sm = 1;
-  const int64_t cap = int64_t(num_sms()) * per_sm / a.pl.G;
+  const int64_t cap = int64_t(num_sms()) / a.pl.G;
   int64_t slots = cap < ntiles ? cap : ntiles;
   if (slots < 1) slots = 1;
   a.slots = int(slots);
   a.sqrtm_f = float(p.sqrtm);
   a.invw_f = float(1.0 / p.w);
   const bool srp = kind_is_srp(p.kind);
-  const dim3 grid((unsigned)(a.slots * a.pl.G)), block((unsigned)(a.pl.W * kWarp));
-  cudaError_t e;
-  if (srp) {
-    e = cudaFuncSetAttribute(sketch_dense_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             a.pl.smem);
-    if (e != cudaSuccess) return e;
-    sketch_dense_kernel<true><<<grid, block, a.pl.smem, stream>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(sketch_dense_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             a.pl.smem);
-    if (e != cudaSuccess) return e;
-    sketch_dense_kernel<false><<<grid, block, a.pl.smem, stream>>>(a);
+  switch (p.dtype) {
+    case LSH_F32: return srp ? launch_t<true, LSH_F32>(a, stream) : launch_t<false, LSH_F32>(a, stream);
+    case LSH_BF16: return srp ? launch_t<true, LSH_BF16>(a, stream) : launch_t<false, LSH_BF16>(a, stream);
+    case LSH_F16: return srp ? launch_t<true, LSH_F16>(a, stream) : launch_t<false, LSH_F16>(a, stream);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lsh

@@ -55,6 +55,11 @@ struct HostFamily {
 // Draw every table of the family from its seed (host, deterministic).
 void sample_family(const lsh_family_desc &desc, HostFamily &hf);
 
+// Largest staged member-list length over the tables of a CS/HCS family: per
+// bin, the coordinates with s = +1 and with s = -1, each rounded up to a
+// multiple of four (the layout of the dense-row hashing kernel).
+int sketch_capacity(const HostFamily &hf);
+
 }  // namespace lsh
 
 struct lsh_family_s {
@@ -69,6 +74,7 @@ struct lsh_family_s {
   float *d_G = nullptr;           // [d][m*L] dense kinds
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
+  int sketch_cap = 0;             // see lsh::sketch_capacity
 };
 
 struct lsh_index_s {
@@ -100,6 +106,7 @@ struct SketchLaunch {
   int32_t kind, m, L, N;
   int32_t dims[LSH_MAX_MODES], mdims[LSH_MAX_MODES];
   int32_t dsum;
+  int32_t cap;           // staged member-list capacity per table (sketch_capacity)
   const uint16_t *bins;
   const int8_t *signs;
   const float *b32;
@@ -120,7 +127,7 @@ struct SketchLaunch {
 cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream);
 // Plan of the dense-row kernel for a shape (for reporting / autotuning).
 struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
-SketchPlan plan_sketch_dense(int d, int m, int L, int dtype);
+SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
 
 // Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
 // Allocates its temporaries with cudaMallocAsync on `stream`.

@@ -125,6 +125,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
     p.mdims[k] = d.mdims[k];
   }
   p.dsum = int32_t(f->host.dsum);
+  p.cap = f->sketch_cap;
   p.bins = f->d_bins;
   p.signs = f->d_signs;
   p.b32 = f->d_b32;
@@ -142,8 +143,10 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.proj = proj;
   p.counters = counters;
   p.status = f->d_status;
-  SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, X->dtype);
+  SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, f->sketch_cap, X->dtype);
   if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
+  if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs
+    LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
   LSH_CUDA_TRY(launch_sketch_dense(p, stream));
   count_launches(1);
   return LSH_OK;
@@ -223,6 +226,7 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
   }
   cudaGetDevice(&f->device);
   const HostFamily &h = f->host;
+  f->sketch_cap = sketch_capacity(h);
   cudaError_t e = cudaSuccess;
   if (!h.bins.empty()) {
     std::vector<uint16_t> b16(h.bins.begin(), h.bins.end());

@@ -57,7 +57,9 @@ def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
         gp = out["proj"][rt].cpu().numpy().astype(np.float64)
         X64 = Xs.detach().cpu().to(torch.float64).numpy()
         scale = np.maximum(np.abs(y), proj_tolerance(X64, m)[:, None, None])
-        rel = float(np.max(np.abs(gp - y) / scale)) if gp.size else 0.0
+        err = np.abs(gp - y)
+        assert (err[scale == 0] == 0).all()  # an all-zero row projects to exact zeros
+        rel = float(np.max(err[scale > 0] / scale[scale > 0])) if (scale > 0).any() else 0.0
         assert rel <= 1e-5, rel
     fam.close()
     return out["stats"], rel
