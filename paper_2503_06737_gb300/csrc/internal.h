@@ -75,6 +75,7 @@ struct lsh_family_s {
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
+  uint16_t *d_colmajor = nullptr; // CS kinds: [d][L] bin | neg << 15 (CSR path)
 };
 
 struct lsh_index_s {
@@ -128,6 +129,11 @@ cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream);
 // Plan of the dense-row kernel for a shape (for reporting / autotuning).
 struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
 SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
+
+// CSR-row CS/HCS hashing (all L tables, one launch).  colmajor: count-sketch
+// tables as [d][L] entries bin | neg << 15 (NULL for HCS).
+cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
+                              const uint16_t *colmajor, cudaStream_t stream);
 
 // Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
 // Allocates its temporaries with cudaMallocAsync on `stream`.

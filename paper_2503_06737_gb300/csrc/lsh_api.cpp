@@ -77,6 +77,7 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_kb);
   cudaFree(f->d_G);
   cudaFree(f->d_status);
+  cudaFree(f->d_colmajor);
   delete f;
 }
 
@@ -108,8 +109,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   const lsh_family_desc &d = f->host.desc;
   if (X->n == 0) return LSH_OK;
   if (kind_is_dense(d.kind)) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP hashing is not in this build yet");
-  if (X->rowptr) return fail(LSH_EUNSUPPORTED, "CSR hashing is not in this build yet");
-  if (X->dtype == LSH_FP8_E4M3) return fail(LSH_EUNSUPPORTED, "FP8 input is for the dense kinds");
+  if (X->dtype == LSH_FP8_E4M3 && !X->rowptr) return fail(LSH_EUNSUPPORTED, "FP8 input is for the dense kinds");
   SketchLaunch p{};
   p.X = X->values;
   p.dtype = X->dtype;
@@ -143,6 +143,14 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.proj = proj;
   p.counters = counters;
   p.status = f->d_status;
+  if (X->rowptr) {
+    if (d.N == 1 && d.m > 32768) return fail(LSH_EUNSUPPORTED, "CSR count-sketch path needs m <= 32768");
+    if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
+    LSH_CUDA_TRY(launch_sketch_csr(p, X->rowptr, X->col, static_cast<const float *>(X->values), f->d_colmajor,
+                                   stream));
+    count_launches(1);
+    return LSH_OK;
+  }
   SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, f->sketch_cap, X->dtype);
   if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
   if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs
@@ -240,6 +248,16 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
   if (e == cudaSuccess) e = upload(&f->d_ka, h.ka.data(), h.ka.size());
   if (e == cudaSuccess) e = upload(&f->d_kb, h.kb.data(), h.kb.size());
   if (e == cudaSuccess && !h.G.empty()) e = upload(&f->d_G, h.G.data(), h.G.size());
+  if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {
+    // column-major copy of the count-sketch tables for the CSR kernel
+    std::vector<uint16_t> cm(size_t(d.d) * d.L);
+    for (int t = 0; t < d.L; ++t)
+      for (int j = 0; j < d.d; ++j) {
+        const size_t src = size_t(t) * h.dsum + j;
+        cm[size_t(j) * d.L + t] = uint16_t(h.bins[src] | (h.signs[src] < 0 ? 0x8000 : 0));
+      }
+    e = upload(&f->d_colmajor, cm.data(), cm.size());
+  }
   if (e == cudaSuccess) e = cudaMalloc(&f->d_status, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(f->d_status, 0, sizeof(uint32_t));
   if (e != cudaSuccess) {
