@@ -270,6 +270,31 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
 
 void lsh_index_destroy(lsh_index_t idx);
 
+/*
+ * Allocation-free table build.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run
+ * (a serving loop with a fixed memory budget, a process whose framework
+ * allocator already holds nearly all of the GPU, a hot path that must never
+ * stall in an allocator).  It does what lsh_build_index does after hashing --
+ * per table, a stable sort of (key, id) and the bucket segmentation -- with
+ * its sort scratch in a 24 MiB array of static device memory that every GPU
+ * loading this library holds until the process exits.  It calls no cudaMalloc
+ * or cudaFree.
+ *   keys      device uint64 [L][n], e.g. the keys output of lsh_hash.
+ *   ids, ukeys, offsets, nbuckets
+ *             device outputs laid out as in lsh_index_export ([L][n], [L][n],
+ *             [L][n+1], [L]); the caller owns them.
+ *   Limits: n * L <= LSH_STATIC_MAX_PAIRS (2^20); larger requests return
+ *   LSH_EINVAL with a message.  The first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.  Every call uses the same
+ *   array and leaves its contents behind, so calls that overlap on the GPU
+ *   (different streams, or different host threads) race; serialise them.
+ */
+#define LSH_STATIC_MAX_PAIRS (1 << 20)
+lsh_status lsh_build_tables_static(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids, uint64_t *ukeys,
+                                   uint32_t *offsets, int64_t *nbuckets, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

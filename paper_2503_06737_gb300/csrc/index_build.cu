@@ -291,4 +291,53 @@ cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *i
   return e;
 }
 
+size_t build_tables_scratch_bytes(int64_t n, int32_t L) {
+  if (n <= 0 || L <= 0) return 0;
+  const size_t ntiles = size_t((n + kTile - 1) / kTile);
+  const size_t nk = size_t(n) * L;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return up(nk * 8) + up(nk * 8) + up(nk * 4) + up(size_t(kRadix) * ntiles * L * 4);
+}
+
+cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
+                                 uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out, void *scratch,
+                                 cudaStream_t stream) {
+  if (L <= 0) return cudaSuccess;
+  if (n == 0) return cudaMemsetAsync(nb_out, 0, sizeof(int64_t) * L, stream);
+  const int ntiles = int((n + kTile - 1) / kTile);
+  const size_t nk = size_t(n) * L;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  unsigned char *base = static_cast<unsigned char *>(scratch);
+  uint64_t *kA = reinterpret_cast<uint64_t *>(base);
+  uint64_t *kB = reinterpret_cast<uint64_t *>(base + up(nk * 8));
+  uint32_t *iA = reinterpret_cast<uint32_t *>(base + 2 * up(nk * 8));
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base + 2 * up(nk * 8) + up(nk * 4));
+  const size_t hist_len = size_t(kRadix) * ntiles;
+  const int scatter_smem = kTile * 12 + (kWarps * kRadix + 2 * kRadix + 33) * 4;
+  cudaError_t e = cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem);
+  const uint64_t *kin = keys;
+  const uint32_t *iin = nullptr;
+  for (int pass = 0; pass < 8 && e == cudaSuccess; ++pass) {
+    uint64_t *kout = (pass % 2 == 0) ? kA : kB;
+    uint32_t *iout = (pass % 2 == 0) ? iA : ids_out;
+    const dim3 grid((unsigned)ntiles, (unsigned)L);
+    radix_hist<<<grid, kThreads, 0, stream>>>(kin, n, pass * 8, ntiles, hist);
+    scan_rows<<<L, 1024, 0, stream>>>(hist, int64_t(hist_len), nullptr);
+    radix_scatter<<<grid, kThreads, scatter_smem, stream>>>(kin, iin, kout, iout, n, pass * 8, ntiles, hist);
+    e = cudaGetLastError();
+    count_launches(3);
+    kin = kout;
+    iin = iout;
+  }
+  if (e == cudaSuccess) {
+    const dim3 grid((unsigned)ntiles, (unsigned)L);
+    seg_count<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, hist);
+    scan_rows<<<L, 1024, 0, stream>>>(hist, ntiles, nb_out);
+    seg_write<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, hist, nb_out, ukeys_out, offsets_out);
+    e = cudaGetLastError();
+    count_launches(3);
+  }
+  return e;
+}
+
 }  // namespace lsh

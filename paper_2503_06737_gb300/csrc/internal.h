@@ -60,6 +60,13 @@ void sample_family(const lsh_family_desc &desc, HostFamily &hf);
 // multiple of four (the layout of the dense-row hashing kernel).
 int sketch_capacity(const HostFamily &hf);
 
+// The same table build with caller-provided scratch (no allocation); the
+// scratch must hold build_tables_scratch_bytes(n, L) bytes, 256-byte aligned.
+size_t build_tables_scratch_bytes(int64_t n, int32_t L);
+cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
+                                 uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out, void *scratch,
+                                 cudaStream_t stream);
+
 }  // namespace lsh
 
 struct lsh_family_s {
@@ -140,5 +147,12 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
 cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
                          uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out,
                          cudaStream_t stream);
+
+// The same table build with caller-provided scratch (no allocation); the
+// scratch must hold build_tables_scratch_bytes(n, L) bytes, 256-byte aligned.
+size_t build_tables_scratch_bytes(int64_t n, int32_t L);
+cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
+                                 uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out, void *scratch,
+                                 cudaStream_t stream);
 
 }  // namespace lsh

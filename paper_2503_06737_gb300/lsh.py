@@ -86,6 +86,7 @@ SIGNATURES = [
     ("lsh_query", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, P, P,
                                  ctypes.POINTER(QueryStats), P]),
     ("lsh_index_destroy", None, [P]),
+    ("lsh_build_tables_static", ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P]),
 ]
 
 
