@@ -142,6 +142,11 @@ SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
                               const uint16_t *colmajor, cudaStream_t stream);
 
+// Query path: probe + dedup + exact top-k rerank, one CTA per query.
+cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
+                         const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
+                         float *out_dist, unsigned long long *counters, cudaStream_t stream);
+
 // Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
 // Allocates its temporaries with cudaMallocAsync on `stream`.
 cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,

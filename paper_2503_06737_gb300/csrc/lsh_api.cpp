@@ -446,15 +446,61 @@ lsh_status lsh_index_export(lsh_index_t idx, uint32_t *ids, uint64_t *ukeys, uin
 }
 
 lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *ids, float *dist,
-                     lsh_query_stats *stats, void *stream) {
+                     lsh_query_stats *stats, void *stream_) {
   if (!idx || !Q) return fail(LSH_EINVAL, "NULL argument");
-  (void)Q;
-  (void)k;
-  (void)ids;
-  (void)dist;
-  (void)stats;
-  (void)stream;
-  return fail(LSH_EUNSUPPORTED, "lsh_query is not in this build yet");
+  lsh_status st = validate_matrix(idx->fam, Q, false);
+  if (st != LSH_OK) return st;
+  if (k < 1 || k > 256) return fail(LSH_EINVAL, "k must be in [1, 256]");
+  if (!idx->d_data && idx->n > 0) return fail(LSH_EINVAL, "the index was built without keep_data");
+  if (Q->n > 0 && (!ids || !dist)) return fail(LSH_EINVAL, "NULL output");
+  if (Q->dtype == LSH_FP8_E4M3) return fail(LSH_EUNSUPPORTED, "FP8 queries are not supported");
+  const lsh_family_desc &d = idx->fam->host.desc;
+  if (d.L > 128) return fail(LSH_EUNSUPPORTED, "lsh_query supports L <= 128");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int64_t q = Q->n;
+  if (q == 0) return LSH_OK;
+  keep_pool_warm();
+  uint64_t *qkeys = nullptr;
+  unsigned long long *cnt = nullptr;
+  LSH_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&qkeys), sizeof(uint64_t) * size_t(q) * d.L, stream));
+  cudaError_t e = cudaSuccess;
+  if (stats) {
+    e = cudaMallocAsync(reinterpret_cast<void **>(&cnt), 4 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), stream);
+  }
+  if (e == cudaSuccess) st = hash_impl(idx->fam, Q, nullptr, qkeys, q, nullptr, nullptr, stream);
+  else st = cuda_fail(e, "lsh_query temporaries");
+  if (st == LSH_OK && idx->n > 0) {
+    e = launch_query(qkeys, q, d.L, k, kind_is_srp(d.kind) ? 1 : 0, d.d, Q->values, Q->dtype, Q->ld, idx, ids,
+                     dist, cnt, stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "lsh_query launch");
+    else count_launches(1);
+  } else if (st == LSH_OK) {
+    // empty index: no candidates
+    std::vector<int32_t> none(size_t(q) * k, -1);
+    std::vector<float> inf(size_t(q) * k, INFINITY);
+    e = cudaMemcpyAsync(ids, none.data(), none.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dist, inf.data(), inf.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "lsh_query empty index");
+  }
+  unsigned long long h[4] = {};
+  if (stats && cnt && st == LSH_OK) {
+    e = cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "lsh_query stats");
+  }
+  cudaFreeAsync(qkeys, stream);
+  if (cnt) cudaFreeAsync(cnt, stream);
+  if (stats && st == LSH_OK) {
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lsh_query sync");
+    stats->n_queries = q;
+    stats->n_candidates = int64_t(h[0]);
+    stats->n_unique = int64_t(h[1]);
+    stats->max_unique = int64_t(h[2]);
+  }
+  return st;
 }
 
 void lsh_index_destroy(lsh_index_t idx) {

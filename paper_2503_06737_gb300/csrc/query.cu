@@ -1,0 +1,354 @@
+// query.cu -- the query path of the (m, tau)-amplified LSH scheme (Sec. 3.1)
+// with the exact rerank of Sec. 6: probe every table with the query's key,
+// take the union of those buckets, rank the distinct candidates by exact
+// distance and keep the k best by (distance, id).
+//
+// One CTA per query, fused:
+//   probe   thread t binary-searches the query's key in the sorted distinct
+//           keys of table t -> (start, count) of its bucket;
+//   gather  the union, flattened over tables, is processed in chunks of up
+//           to kCap ids staged in shared memory;
+//   dedup   each chunk is bitonic-sorted and compacted to distinct ids;
+//   rerank  one warp per candidate: FP32 distance from the index's copy of
+//           the data row (Euclidean for E2LSH kinds, 1 - cos for SRP kinds);
+//   top-k   merged into a running (distance, id) list.  An id that repeats in
+//           a later chunk has the same distance: if it is in the list it is
+//           skipped, and if it is not, it lost against a list that has only
+//           improved since, so it cannot enter -- the union is deduplicated
+//           exactly without a global sort.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace lsh {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kCap = 4096;  // candidate ids per chunk
+constexpr int kMaxL = 128;
+constexpr int kMaxK = 256;
+
+struct QueryArgs {
+  const uint64_t *qkeys;  // [L][q]
+  int64_t q;
+  int32_t L, k, metric, d;
+  const void *Q;
+  int32_t q_dtype;
+  int64_t q_ld;
+  const uint32_t *ids;     // [L][n]
+  const uint64_t *ukeys;   // [L][n]
+  const uint32_t *offsets; // [L][n+1]
+  const int64_t *nb;       // [L]
+  int64_t n;
+  const void *X;
+  int32_t x_dtype;
+  int64_t x_ld;
+  int32_t *out_ids;
+  float *out_dist;
+  unsigned long long *counters;  // [4]: candidates, unique, max unique (atomicMax), queries
+};
+
+__device__ __forceinline__ float ld_elem(const void *p, int dtype, int64_t idx) {
+  if (dtype == LSH_F32) return __ldg(reinterpret_cast<const float *>(p) + idx);
+  const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(p) + idx);
+  if (dtype == LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
+  return __half2float(__ushort_as_half(h));
+}
+
+__device__ __forceinline__ bool better(float da, uint32_t ia, float db, uint32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
+__global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float *qv = reinterpret_cast<float *>(sm);                       // [d]
+  uint32_t *bstart = reinterpret_cast<uint32_t *>(qv + a.d);       // [L]
+  uint32_t *pre = bstart + kMaxL;                                  // [L+1]
+  uint32_t *cand = pre + kMaxL + 1;                                // [kCap]
+  float *cdist = reinterpret_cast<float *>(cand + kCap);           // [kCap]
+  float *topd = cdist + kCap;                                      // [k]
+  uint32_t *topi = reinterpret_cast<uint32_t *>(topd + kMaxK);     // [k]
+  __shared__ uint32_t wsum[kThreads / 32 + 1];
+  __shared__ float red_d[kThreads / 32];
+  __shared__ uint32_t red_i[kThreads / 32];
+  __shared__ int red_s[kThreads / 32];
+  __shared__ float qnorm2;
+
+  const int64_t qi = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int L = a.L, k = a.k, d = a.d;
+
+  // query row in FP32 and its squared norm
+  float part = 0.f;
+  for (int j = tid; j < d; j += kThreads) {
+    const float v = ld_elem(a.Q, a.q_dtype, qi * a.q_ld + j);
+    qv[j] = v;
+    part += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) red_d[warp] = part;
+  // probe: table t -> bucket (start, count)
+  for (int t = tid; t < L; t += kThreads) {
+    const uint64_t key = a.qkeys[int64_t(t) * a.q + qi];
+    const uint64_t *uk = a.ukeys + int64_t(t) * a.n;
+    int64_t lo = 0, hi = a.nb[t];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (uk[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    uint32_t s = 0, c = 0;
+    if (lo < a.nb[t] && uk[lo] == key) {
+      const uint32_t *of = a.offsets + int64_t(t) * (a.n + 1);
+      s = of[lo];
+      c = of[lo + 1] - s;
+    }
+    bstart[t] = s;
+    pre[t + 1] = c;
+  }
+  for (int r = tid; r < k; r += kThreads) {
+    topd[r] = __int_as_float(0x7f800000);
+    topi[r] = 0xffffffffu;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) s += red_d[w];
+    qnorm2 = s;
+    pre[0] = 0;
+    for (int t = 0; t < L; ++t) pre[t + 1] += pre[t];
+  }
+  __syncthreads();
+  const uint32_t C = pre[L];
+  uint32_t uniq_total = 0, uniq_max = 0;
+
+  for (uint32_t c0 = 0; c0 < C; c0 += kCap) {
+    const uint32_t cc = min(uint32_t(kCap), C - c0);
+    uint32_t P = 1;
+    while (P < cc) P <<= 1;
+    // gather the chunk (flat index over tables)
+    for (uint32_t f = tid; f < P; f += kThreads) {
+      uint32_t id = 0xffffffffu;
+      if (f < cc) {
+        const uint32_t g = c0 + f;
+        int lo = 0, hi = L;  // last t with pre[t] <= g
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pre[mid] <= g) lo = mid; else hi = mid;
+        }
+        id = a.ids[int64_t(lo) * a.n + bstart[lo] + (g - pre[lo])];
+      }
+      cand[f] = id;
+    }
+    __syncthreads();
+    // bitonic sort of cand[0..P)
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t i = tid; i < P; i += kThreads) {
+          const uint32_t j = i ^ stride;
+          if (j > i) {
+            const uint32_t x = cand[i], y = cand[j];
+            const bool up = (i & size) == 0;
+            if ((x > y) == up) {
+              cand[i] = y;
+              cand[j] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // compact distinct ids into cdist (reused as u32) with a block scan
+    uint32_t *uq = reinterpret_cast<uint32_t *>(cdist);
+    const uint32_t per = (cc + kThreads - 1) / kThreads;
+    const uint32_t b0 = tid * per, b1 = min(cc, b0 + per);
+    uint32_t cnt = 0;
+    for (uint32_t f = b0; f < b1; ++f) cnt += (f == 0 || cand[f] != cand[f - 1]) ? 1u : 0u;
+    uint32_t s = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += u;
+    }
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const uint32_t v = wsum[w];
+        wsum[w] = run;
+        run += v;
+      }
+      wsum[kThreads / 32] = run;
+    }
+    __syncthreads();
+    uint32_t pos = wsum[warp] + s - cnt;
+    const uint32_t U = wsum[kThreads / 32];
+    __syncthreads();  // everyone has read cand boundaries' scan before uq is written
+    for (uint32_t f = b0; f < b1; ++f)
+      if (f == 0 || cand[f] != cand[f - 1]) uq[pos++] = cand[f];
+    __syncthreads();
+    // move distinct ids to the front of cand, distances into cdist
+    for (uint32_t u = tid; u < U; u += kThreads) cand[u] = uq[u];
+    __syncthreads();
+    uniq_total += U;
+    uniq_max = max(uniq_max, U);
+    // distances: one warp per candidate
+    for (uint32_t u = warp; u < U; u += kThreads / 32) {
+      const uint32_t id = cand[u];
+      const int64_t base = int64_t(id) * a.x_ld;
+      float acc = 0.f, xx = 0.f;
+      for (int j = lane; j < d; j += 32) {
+        const float x = ld_elem(a.X, a.x_dtype, base + j);
+        if (a.metric == 0) {
+          const float e = qv[j] - x;
+          acc = fmaf(e, e, acc);
+        } else {
+          acc = fmaf(qv[j], x, acc);
+          xx = fmaf(x, x, xx);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+      }
+      if (lane == 0) {
+        float dist;
+        if (a.metric == 0) {
+          dist = sqrtf(acc);
+        } else {
+          dist = (qnorm2 > 0.f && xx > 0.f) ? 1.f - acc / (sqrtf(qnorm2) * sqrtf(xx)) : 1.f;
+        }
+        cdist[u] = dist;
+      }
+    }
+    __syncthreads();
+    // drop candidates already in the top-k list (same id => same distance)
+    for (uint32_t u = tid; u < U; u += kThreads) {
+      const uint32_t id = cand[u];
+      for (int r = 0; r < k; ++r)
+        if (topi[r] == id) {
+          cdist[u] = __int_as_float(0x7f800000);
+          cand[u] = 0xffffffffu;
+          break;
+        }
+    }
+    __syncthreads();
+    // merge: k rounds of block argmin over (list entries not yet taken) U (chunk)
+    // list and chunk entries are tagged by source; the new list is built in place
+    // in registers of thread 0 via shared buffers.
+    {
+      // candidates: list slots r (source 1) and chunk slots u (source 0)
+      __shared__ float newd[kMaxK];
+      __shared__ uint32_t newi[kMaxK];
+      for (int r = 0; r < k; ++r) {
+        float bd = __int_as_float(0x7f800000);
+        uint32_t bi = 0xffffffffu;
+        int bs = -1;  // encoded slot: >= 0 chunk index, < -1 list index (-(r)-2)
+        for (uint32_t u = tid; u < U; u += kThreads)
+          if (cand[u] != 0xffffffffu && better(cdist[u], cand[u], bd, bi)) {
+            bd = cdist[u];
+            bi = cand[u];
+            bs = int(u);
+          }
+        for (int rr = tid; rr < k; rr += kThreads)
+          if (topi[rr] != 0xffffffffu && better(topd[rr], topi[rr], bd, bi)) {
+            bd = topd[rr];
+            bi = topi[rr];
+            bs = -rr - 2;
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+          const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+          if (better(od, oi, bd, bi)) {
+            bd = od;
+            bi = oi;
+            bs = os;
+          }
+        }
+        if (lane == 0) {
+          red_d[warp] = bd;
+          red_i[warp] = bi;
+          red_s[warp] = bs;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          float fd = red_d[0];
+          uint32_t fi = red_i[0];
+          int fs = red_s[0];
+          for (int w = 1; w < kThreads / 32; ++w)
+            if (better(red_d[w], red_i[w], fd, fi)) {
+              fd = red_d[w];
+              fi = red_i[w];
+              fs = red_s[w];
+            }
+          newd[r] = fd;
+          newi[r] = fi;
+          if (fs >= 0) cand[fs] = 0xffffffffu;             // taken from the chunk
+          else if (fs <= -2) topi[-fs - 2] = 0xffffffffu;  // taken from the list
+        }
+        __syncthreads();
+      }
+      for (int r = tid; r < k; r += kThreads) {
+        topd[r] = newd[r];
+        topi[r] = newi[r];
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = tid; r < k; r += kThreads) {
+    const bool ok = topi[r] != 0xffffffffu;
+    a.out_ids[qi * k + r] = ok ? int32_t(topi[r]) : -1;
+    a.out_dist[qi * k + r] = ok ? topd[r] : __int_as_float(0x7f800000);
+  }
+  if (tid == 0 && a.counters) {
+    atomicAdd(a.counters + 0, (unsigned long long)C);
+    atomicAdd(a.counters + 1, (unsigned long long)uniq_total);
+    atomicMax(a.counters + 2, (unsigned long long)uniq_max);
+    atomicAdd(a.counters + 3, 1ull);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
+                         const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
+                         float *out_dist, unsigned long long *counters, cudaStream_t stream) {
+  if (q <= 0) return cudaSuccess;
+  if (L > kMaxL || k > kMaxK) return cudaErrorInvalidValue;
+  QueryArgs a{};
+  a.qkeys = qkeys;
+  a.q = q;
+  a.L = L;
+  a.k = k;
+  a.metric = metric;
+  a.d = d;
+  a.Q = Q;
+  a.q_dtype = q_dtype;
+  a.q_ld = q_ld;
+  a.ids = idx->d_ids;
+  a.ukeys = idx->d_ukeys;
+  a.offsets = idx->d_offsets;
+  a.nb = idx->d_nb;
+  a.n = idx->n;
+  a.X = idx->d_data;
+  a.x_dtype = idx->data_dtype;
+  a.x_ld = idx->data_ld;
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.counters = counters;
+  const int smem = d * 4 + (2 * kMaxL + 1) * 4 + kCap * 8 + kMaxK * 8;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (q > INT32_MAX) return cudaErrorInvalidValue;
+  query_kernel<<<(unsigned)q, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace lsh

@@ -1,0 +1,125 @@
+"""GPU parity of lsh_query (probe, union of buckets, exact FP32 rerank, top-k)
+against the oracle's FP64 query path on the same seeded data.
+
+The candidate set is decided by integer keys, so it is identical on both
+sides; distances differ only by FP32 rounding.  The checks: the sorted FP64
+distances of the GPU's ids equal the oracle's top-k distances within 1e-5
+relative; every GPU id the oracle did not return ties the oracle's k-th
+distance within that tolerance; each reported FP32 distance is within 1e-5
+relative of the FP64 distance of its id; missing slots are (-1, +inf).  Cases
+span Euclidean and cosine metrics, f32 and f16 data, k = 1..256, queries with
+no candidate, candidate unions far larger than one shared-memory chunk, and
+the 10,000 x 128 workload with 100 noisy queries.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_06737_gb300 import lsh, workloads
+
+from gpu_helpers import to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _dist64(Xh, Qh, ids, metric):
+    X = Xh.astype(np.float64)
+    q = Qh.astype(np.float64)
+    if metric == 0:
+        return np.sqrt(((X[ids] - q) ** 2).sum(-1))
+    xn = np.linalg.norm(X[ids], axis=-1)
+    qn = np.linalg.norm(q)
+    return 1 - (X[ids] @ q) / (xn * qn)
+
+
+def _run(args, X, Q, k, tol=1e-5):
+    fam = lsh.Family(**args)
+    idx = fam.build_index(X, keep_data=True)
+    out = idx.query(Q, k=k, stats=True)
+    torch.cuda.synchronize()
+    gids = out["ids"].cpu().numpy()
+    gdist = out["dist"].cpu().numpy().astype(np.float64)
+    Xh, dt = to_oracle(X)
+    Qh, dtq = to_oracle(Q)
+    of = oracle.family(args["kind"], args["d"], args["m"], args["L"], w=args.get("w", 4.0),
+                       seed=args.get("seed", 42), dims=args.get("dims"), mdims=args.get("mdims"))
+    _, _, _, keys = oracle.hash_dense(of, Xh, dtype=dt, want_y=False, want_codes=False)
+    _, _, _, qkeys = oracle.hash_dense(of, Qh, dtype=dtq, want_y=False, want_codes=False)
+    oidx = oracle.build_index(keys)
+    metric = 1 if fam.is_srp else 0
+    oids, odist, ncand = oracle.query(oidx, args["d"], Xh, Qh, qkeys, k, metric, dtype=dt, dtype_q=dtq)
+    X64 = X.detach().cpu().to(torch.float64).numpy()
+    Q64 = Q.detach().cpu().to(torch.float64).numpy()
+    for i in range(Q.shape[0]):
+        nvalid = int((oids[i] >= 0).sum())
+        assert int((gids[i] >= 0).sum()) == nvalid
+        assert (gids[i, nvalid:] == -1).all() and np.isinf(gdist[i, nvalid:]).all()
+        if nvalid == 0:
+            continue
+        g = gids[i, :nvalid]
+        assert len(set(g.tolist())) == nvalid  # distinct
+        d64 = _dist64(X64, Q64[i], g, metric)
+        scale = np.maximum(np.abs(odist[i, :nvalid]), 1e-6)
+        assert np.all(np.abs(np.sort(d64) - odist[i, :nvalid]) <= tol * scale + 1e-6), i
+        assert np.all(np.abs(gdist[i, :nvalid] - d64) <= tol * np.maximum(np.abs(d64), 1e-6) + 1e-6)
+        extra = set(g.tolist()) - set(oids[i, :nvalid].tolist())
+        kth = odist[i, nvalid - 1]
+        for e in extra:
+            de = _dist64(X64, Q64[i], np.array([e]), metric)[0]
+            assert abs(de - kth) <= tol * max(abs(kth), 1e-6) + 1e-6
+    return out["stats"], ncand, gids, oids
+
+
+@pytest.mark.parametrize("kind,metric_dims", [("cs_e2lsh", None), ("cs_srp", None),
+                                              ("hcs_e2lsh", ([8, 16], [4, 4])), ("hcs_srp", ([8, 16], [4, 4]))])
+def test_query_small_workload(kind, metric_dims):
+    wl = workloads.WORKLOADS["iid_10k_d128"]
+    X = workloads.iid(wl["n"], wl["d"], seed=1234, device="cpu").cuda()
+    Q, src = workloads.noisy_queries(X, wl["queries"], wl["query_sigma"], seed=7)
+    dims, mdims = metric_dims if metric_dims else (None, None)
+    args = dict(kind=kind, d=128, m=16, L=10, w=wl["w"], seed=42, dims=dims, mdims=mdims)
+    stats, ncand, gids, oids = _run(args, X, Q, k=10)
+    assert stats["n_queries"] == wl["queries"]
+    if stats["max_unique"] <= 4096:
+        assert stats["n_unique"] == int(ncand.sum())
+    # whenever the noisy copy's source point is a candidate it is the nearest
+    # (distance ~1.1 against ~16 for any other point of this workload)
+    s = src.cpu().numpy()
+    found = np.array([s[i] in oids[i] for i in range(len(s))])
+    assert found.any()
+    assert (gids[found, 0] == s[found]).all()
+
+
+def test_query_f16_data_and_k_range():
+    X = workloads.gmm(5000, 128, 32, seed=5, device="cpu", dtype=torch.float16).cuda()
+    Q, _ = workloads.noisy_queries(X, 33, 0.05, seed=8)
+    args = dict(kind="hcs_e2lsh", d=128, m=16, L=12, w=6.0, seed=3, dims=[8, 16], mdims=[4, 4])
+    for k in (1, 10, 256):
+        _run(args, X, Q, k=k)
+
+
+def test_query_large_unions_span_chunks():
+    # very wide bins and m = 2: buckets hold most points, unions far exceed a chunk
+    X = workloads.iid(20000, 32, seed=9, device="cpu").cuda()
+    Q, _ = workloads.noisy_queries(X, 8, 0.1, seed=10)
+    args = dict(kind="cs_e2lsh", d=32, m=2, L=6, w=64.0, seed=4)
+    stats, ncand, _, _ = _run(args, X, Q, k=20)
+    assert stats["max_unique"] > 0 and int(ncand.max()) > 4096
+
+
+def test_query_without_candidates():
+    X = workloads.iid(3000, 64, seed=11, device="cpu").cuda()
+    Q = torch.full((3, 64), 1e6, device="cuda")  # far from every bucket
+    Q[1] = X[5]
+    args = dict(kind="cs_e2lsh", d=64, m=16, L=4, w=1.0, seed=6)
+    _, _, gids, _ = _run(args, X, Q, k=5)
+    assert (gids[0] == -1).all() and (gids[2] == -1).all() and gids[1, 0] == 5
+
+
+def test_query_needs_kept_data():
+    X = workloads.iid(100, 16, seed=1, device="cpu").cuda()
+    fam = lsh.Family("cs_e2lsh", 16, 4, 2)
+    idx = fam.build_index(X, keep_data=False)
+    with pytest.raises(lsh.LshError):
+        idx.query(X[:2], k=3)
