@@ -79,6 +79,8 @@ struct lsh_family_s {
   uint32_t *d_ka = nullptr;       // [L][m]
   uint32_t *d_kb = nullptr;       // [L][m]
   float *d_G = nullptr;           // [d][m*L] dense kinds
+  float *d_Gt = nullptr;          // [m*L][d] transposed copy (FP64 recheck reads columns)
+  float *d_gnorm = nullptr;       // [m*L] column norms, rounded up
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
@@ -141,6 +143,11 @@ SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
 // tables as [d][L] entries bin | neg << 15 (NULL for HCS).
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
                               const uint16_t *colmajor, cudaStream_t stream);
+
+// Dense E2LSH / SRP (FP32 SIMT GEMM, fused discretisation and recheck).
+// keys and multi-word SRP bits must be zeroed by the caller.
+cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float *Gt, const float *gnorm,
+                              cudaStream_t stream);
 
 // Query path: probe + dedup + exact top-k rerank, one CTA per query.
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,

@@ -76,6 +76,8 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_ka);
   cudaFree(f->d_kb);
   cudaFree(f->d_G);
+  cudaFree(f->d_Gt);
+  cudaFree(f->d_gnorm);
   cudaFree(f->d_status);
   cudaFree(f->d_colmajor);
   delete f;
@@ -108,7 +110,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
                      float *proj, unsigned long long *counters, cudaStream_t stream) {
   const lsh_family_desc &d = f->host.desc;
   if (X->n == 0) return LSH_OK;
-  if (kind_is_dense(d.kind)) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP hashing is not in this build yet");
+  if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
   if (X->dtype == LSH_FP8_E4M3 && !X->rowptr) return fail(LSH_EUNSUPPORTED, "FP8 input is for the dense kinds");
   SketchLaunch p{};
   p.X = X->values;
@@ -143,6 +145,13 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.proj = proj;
   p.counters = counters;
   p.status = f->d_status;
+  if (kind_is_dense(d.kind)) {
+    if (keys) LSH_CUDA_TRY(cudaMemsetAsync(keys, 0, sizeof(uint64_t) * size_t(key_ld) * d.L, stream));
+    if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
+    LSH_CUDA_TRY(launch_dense_fp32(p, f->d_G, f->d_Gt, f->d_gnorm, stream));
+    count_launches(1);
+    return LSH_OK;
+  }
   if (X->rowptr) {
     if (d.N == 1 && d.m > 32768) return fail(LSH_EUNSUPPORTED, "CSR count-sketch path needs m <= 32768");
     if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
@@ -247,7 +256,22 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
   if (e == cudaSuccess) e = upload(&f->d_b64, h.b.data(), h.b.size());
   if (e == cudaSuccess) e = upload(&f->d_ka, h.ka.data(), h.ka.size());
   if (e == cudaSuccess) e = upload(&f->d_kb, h.kb.data(), h.kb.size());
-  if (e == cudaSuccess && !h.G.empty()) e = upload(&f->d_G, h.G.data(), h.G.size());
+  if (e == cudaSuccess && !h.G.empty()) {
+    e = upload(&f->d_G, h.G.data(), h.G.size());
+    const size_t ml = size_t(d.m) * d.L;
+    std::vector<float> gt(h.G.size()), gn(ml);
+    for (size_t c = 0; c < ml; ++c) {
+      double s2 = 0.0;
+      for (int j = 0; j < d.d; ++j) {
+        const float g = h.G[size_t(j) * ml + c];
+        gt[c * d.d + j] = g;
+        s2 += double(g) * double(g);
+      }
+      gn[c] = float(std::sqrt(s2) * (1.0 + 1e-6));  // rounded up
+    }
+    if (e == cudaSuccess) e = upload(&f->d_Gt, gt.data(), gt.size());
+    if (e == cudaSuccess) e = upload(&f->d_gnorm, gn.data(), gn.size());
+  }
   if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {
     // column-major copy of the count-sketch tables for the CSR kernel
     std::vector<uint16_t> cm(size_t(d.d) * d.L);

@@ -24,9 +24,12 @@ def unpack_bits(words: np.ndarray, m: int) -> np.ndarray:
     return ((w[..., l // 64] >> (l % 64).astype(np.uint64)) & np.uint64(1)).astype(np.int32)
 
 
-def proj_tolerance(Xh64: np.ndarray, m: int):
-    """Per-row scale for the projection check: 1e-5 relative to max(|y|, ||x||/sqrt(m))."""
-    return np.linalg.norm(Xh64, axis=1) / np.sqrt(m)
+def proj_tolerance(Xh64: np.ndarray, m: int, dense: bool = False):
+    """Per-row scale for the projection check: 1e-5 relative to max(|y|, s), where s
+    is the typical size of a projection: ||x|| / sqrt(m) for a sketch bin (Theorems
+    13, 20), ||x|| for a dense Gaussian projection."""
+    nrm = np.linalg.norm(Xh64, axis=1)
+    return nrm if dense else nrm / np.sqrt(m)
 
 
 def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
@@ -56,7 +59,8 @@ def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
     if check_proj:
         gp = out["proj"][rt].cpu().numpy().astype(np.float64)
         X64 = Xs.detach().cpu().to(torch.float64).numpy()
-        scale = np.maximum(np.abs(y), proj_tolerance(X64, m)[:, None, None])
+        dense = fam_args["kind"] in ("e2lsh", "srp")
+        scale = np.maximum(np.abs(y), proj_tolerance(X64, m, dense)[:, None, None])
         err = np.abs(gp - y)
         assert (err[scale == 0] == 0).all()  # an all-zero row projects to exact zeros
         rel = float(np.max(err[scale > 0] / scale[scale > 0])) if (scale > 0).any() else 0.0

@@ -1,0 +1,56 @@
+"""GPU parity of the dense baselines E2LSH (Definition 2) and SRP (Definition 3):
+FP32 SIMT GEMM with the fused epilogue and FP64 recheck against the oracle's
+FP64 projection x G in ascending j.  Codes and keys bit-exact, projections
+within 1e-5 of max(|y|, ||x||); shapes with ragged row / column tiles, tables
+that straddle CTA tiles (m not dividing 128), f32/bf16/f16 inputs, and the
+index and query path on dense kinds."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_06737_gb300 import lsh, workloads
+
+from gpu_helpers import compare_hash
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+@pytest.mark.parametrize("n,d,m,L,dtype", [
+    (300, 128, 16, 10, torch.float32),
+    (257, 960, 64, 3, torch.float32),
+    (130, 37, 12, 13, torch.float32),   # 156 columns: tables straddle the 128-column tiles
+    (200, 512, 32, 8, torch.bfloat16),
+    (129, 128, 16, 4, torch.float16),
+    (64, 100, 100, 2, torch.float32),   # SRP m > 64: two-word codes
+])
+def test_dense_parity(kind, n, d, m, L, dtype):
+    X = workloads.gmm(n, d, 8, seed=n + d, device="cpu", dtype=dtype).cuda()
+    stats, rel = compare_hash(dict(kind=kind, d=d, m=m, L=L, w=4.0, seed=13), X)
+    assert stats["n_changed"] <= stats["n_flagged"]
+
+
+def test_dense_narrow_bins_exercise_recheck():
+    X = workloads.iid(200, 256, seed=3, device="cpu").cuda()
+    stats, _ = compare_hash(dict(kind="e2lsh", d=256, m=16, L=8, w=0.01, seed=2), X)
+    assert stats["n_flagged"] > 0
+
+
+def test_dense_nonfinite_rows():
+    X = workloads.iid(70, 64, seed=4, device="cpu").cuda()
+    X[3, 5] = float("nan")
+    fam = lsh.Family("e2lsh", 64, 16, 3, seed=1)
+    with pytest.raises(lsh.LshError):
+        fam.hash(X, keys=True, stats=True)
+    k = fam.hash(X, keys=True)["keys"].cpu().numpy().view(np.uint64)
+    assert (k[:, 3] == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    good = torch.as_tensor(np.setdiff1d(np.arange(70), [3])).cuda()
+    compare_hash(dict(kind="e2lsh", d=64, m=16, L=3, seed=1), X[good])
+
+
+def test_dense_index_and_query():
+    from test_gpu_query import _run
+    X = workloads.gmm(4000, 64, 16, seed=6, device="cpu").cuda()
+    Q, _ = workloads.noisy_queries(X, 20, 0.05, seed=9)
+    _run(dict(kind="e2lsh", d=64, m=8, L=6, w=4.0, seed=5), X, Q, k=10)
+    _run(dict(kind="srp", d=64, m=8, L=6, seed=5), X, Q, k=10)
