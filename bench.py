@@ -222,6 +222,81 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
+    """Dense FP32 GEMM baseline at the same m*L, the CSR workload, and the small
+    index + query workload (each timed with CUDA events on the launching stream)."""
+    import torch
+    from paper_2503_06737_gb300 import lsh, workloads
+    out = {}
+    wl, fa = _workload(args.workload, "e2lsh")
+    n, d, L, m = X.shape[0], X.shape[1], fa["L"], fa["m"]
+    mtx = lsh.dense_matrix(X)
+    fd = lsh.Family(**fa)
+    fd.hash_into(mtx, None, lsh._ptr(keys), None)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        fd.hash_into(mtx, None, lsh._ptr(keys), None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dms = e0.elapsed_time(e1) / 3
+    flops = 2.0 * n * d * m * L
+    st = fd.hash(X[:65536], keys=True, stats=True)["stats"]
+    out["dense_fp32_e2lsh"] = {"hash_ms": dms, "points_per_s": n / (dms / 1e3), "tflops": flops / (dms / 1e3) / 1e12,
+                               "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
+                               "note": "FP32 SIMT GEMM x G (d x mL = %d x %d) + fused epilogue, same m*L" % (d, m * L)}
+    fd.close()
+    # CSR workload: 200,000 x 20,000 at 1%, m = 256, L = 20
+    cw = workloads.WORKLOADS["csr_200k_d20000"]
+    rowptr, cols, vals = workloads.csr_rows(cw["n"], cw["d"], cw["nnz"], seed=1236, device=X.device)
+    ck = torch.empty((cw["L"], cw["n"]), dtype=torch.int64, device=X.device)
+    cm = lsh.csr_matrix(rowptr, cols, vals, cw["d"])
+    for kind, dims, mdims in (("cs_srp", None, None), ("hcs_srp", cw["hcs_dims"], cw["hcs_mdims"])):
+        fc = lsh.Family(kind, cw["d"], cw["m"], cw["L"], seed=42, dims=dims, mdims=mdims)
+        fc.hash_into(cm, None, lsh._ptr(ck), None)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            fc.hash_into(cm, None, lsh._ptr(ck), None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / 10
+        cbytes = float(vals.numel() * 4 + cols.numel() * 4 + rowptr.numel() * 8 + ck.numel() * 8)
+        out["csr_200k_d20000_" + kind] = {"hash_ms": cms, "points_per_s": cw["n"] / (cms / 1e3),
+                                          "hbm_frac": cbytes / (cms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                          "adds_per_s": float(vals.numel()) * cw["L"] / (cms / 1e3)}
+        fc.close()
+    del rowptr, cols, vals, ck
+    # small workload: 10,000 x 128, CS-E2LSH m = 16, L = 10: index build + 100 queries
+    sw = workloads.WORKLOADS["iid_10k_d128"]
+    Xs = workloads.iid(sw["n"], sw["d"], seed=1234, device=X.device)
+    Qs, _ = workloads.noisy_queries(Xs, sw["queries"], sw["query_sigma"], seed=7)
+    fs = lsh.Family("cs_e2lsh", sw["d"], sw["m"], sw["L"], w=sw["w"], seed=42)
+    idx = fs.build_index(Xs, keep_data=True)
+    ms_b = lsh.dense_matrix(Xs)
+    for _ in range(3):
+        idx.rebuild_into(ms_b)
+        idx.query(Qs, k=10)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        idx.rebuild_into(ms_b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / 20
+    e0.record(stream)
+    for _ in range(20):
+        idx.query(Qs, k=10)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qms = e0.elapsed_time(e1) / 20
+    out["iid_10k_d128_build_and_query"] = {"build_us": bms * 1e3, "query_100_us": qms * 1e3,
+                                           "qps": sw["queries"] / (qms / 1e3)}
+    idx.close()
+    fs.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +451,7 @@ def main():
                               "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
                               "changed": st["n_changed"]}
             f2.close()
+        variants.update(extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream))
     clocks.stop()
     clk = clocks.summary(t_wall0, t_wall2)
 

@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
         const uint4 c = C[l];
         const float A = __uint_as_float(c.y);
         if (SRP) {
-          const bool flag = valid && !isbad && !(fabsf(y) > A * xm);
+          // A = 0 when the bin holds at most one term: the FP32 value is then exact
+          const bool flag = valid && !isbad && A > 0.f && !(fabsf(y) > A * xm);
           int bit = y > 0.f ? 1 : 0;
           if (__any_sync(0xffffffffu, flag)) {
             if (flag) {
