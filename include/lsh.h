@@ -271,6 +271,55 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
 void lsh_index_destroy(lsh_index_t idx);
 
 /*
+ * Serving loop (continuous batching) around lsh_query, with the data and the
+ * index resident on the device.  Requests are batches of host queries; a
+ * scheduler thread admits the oldest waiting request whenever one of `slots`
+ * concurrent batch slots is free and the device bytes held by the batches in
+ * flight, plus this request's, stay within `mem_budget`; admitted batches run
+ * concurrently, each on its own stream: H2D -> hash -> probe / dedup / exact
+ * rerank -> D2H.  With use_graphs, each slot captures one CUDA graph per
+ * power-of-two batch bucket (>= 16 rows) and replays it for later batches of
+ * that bucket, the rows beyond the batch being padding whose results are
+ * dropped.  Each query is answered from its own row by its own CTA, so its
+ * result does not depend on the other queries of its batch or of concurrent
+ * batches.  The index (and its family) must outlive the server.
+ */
+typedef struct {
+  int32_t max_batch;   /* largest batch (queries) a request may hold, 1..65536 */
+  int32_t slots;       /* batches in flight at once (streams), 1..64 */
+  int32_t k;           /* top-k of every query, 1..256 */
+  int32_t use_graphs;  /* nonzero: replay captured graphs per batch-size bucket */
+  int64_t mem_budget;  /* device bytes for batches in flight (0: no limit) */
+} lsh_server_config;
+
+typedef struct {
+  int64_t completed_requests, completed_queries;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* request latency, submit -> results on host */
+  double busy_s;                           /* first submit -> last completion (seconds) */
+  int64_t admitted_peak;                   /* most batches in flight at once */
+  int64_t graph_replays, graph_captures;
+} lsh_server_stats;
+
+typedef struct lsh_server_s *lsh_server_t;
+
+/* Start a serving loop on the current device over an index built with keep_data. */
+lsh_status lsh_server_create(lsh_index_t idx, const lsh_server_config *cfg, lsh_server_t *out);
+
+/* Queue a batch: queries = host [q][d] of `dtype` (f32 / bf16 / f16), copied
+ * before the call returns; 1 <= q <= max_batch.  *ticket identifies it. */
+lsh_status lsh_server_submit(lsh_server_t srv, const void *queries, int32_t dtype, int64_t q, int64_t *ticket);
+
+/* Block until the ticket's batch is done; copy ids [q][k] / dist [q][k] to
+ * host buffers (either may be NULL) and its latency in milliseconds. */
+lsh_status lsh_server_wait(lsh_server_t srv, int64_t ticket, int32_t *ids, float *dist, double *latency_ms);
+
+/* Latency percentiles and counters since creation or the last reset. */
+lsh_status lsh_server_stats_get(lsh_server_t srv, lsh_server_stats *stats, int32_t reset);
+
+/* Finish the queued and running batches, then stop. */
+void lsh_server_destroy(lsh_server_t srv);
+
+/*
  * Allocation-free table build.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they run
  * (a serving loop with a fixed memory budget, a process whose framework

@@ -144,6 +144,11 @@ SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
                               const uint16_t *colmajor, cudaStream_t stream);
 
+// Hash the rows of X into keys [L][key_ld] (+ optional codes, proj, counters);
+// stream-ordered, allocates nothing when counters is NULL.
+lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
+                     float *proj, unsigned long long *counters, cudaStream_t stream);
+
 // Dense E2LSH / SRP (FP32 SIMT GEMM, fused discretisation and recheck).
 // keys and multi-word SRP bits must be zeroed by the caller.
 cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float *Gt, const float *gnorm,

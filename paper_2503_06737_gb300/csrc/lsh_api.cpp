@@ -105,6 +105,8 @@ lsh_status validate_matrix(const lsh_family_s *f, const lsh_matrix *X, bool allo
 
 size_t dtype_size(int dt) { return dt == LSH_F32 ? 4 : (dt == LSH_FP8_E4M3 ? 1 : 2); }
 
+}  // namespace
+
 // Hash into keys [L][key_ld] (and the optional outputs).  Stream-ordered.
 lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
                      float *proj, unsigned long long *counters, cudaStream_t stream) {
@@ -168,6 +170,8 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   count_launches(1);
   return LSH_OK;
 }
+
+namespace {
 
 lsh_family_desc normalized(const lsh_family_desc &in) {
   lsh_family_desc d = in;

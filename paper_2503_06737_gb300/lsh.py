@@ -64,6 +64,22 @@ class QueryStats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("mem_budget", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed_requests", ctypes.c_int64), ("completed_queries", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("busy_s", ctypes.c_double), ("admitted_peak", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("graph_captures", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: (float(getattr(self, k)) if t is ctypes.c_double else int(getattr(self, k)))
+                for k, t in self._fields_}
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported symbol of include/lsh.h
@@ -87,6 +103,11 @@ SIGNATURES = [
                                  ctypes.POINTER(QueryStats), P]),
     ("lsh_index_destroy", None, [P]),
     ("lsh_build_tables_static", ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P]),
+    ("lsh_server_create", ctypes.c_int, [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
+    ("lsh_server_submit", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    ("lsh_server_wait", ctypes.c_int, [P, ctypes.c_int64, P, P, ctypes.POINTER(ctypes.c_double)]),
+    ("lsh_server_stats_get", ctypes.c_int, [P, ctypes.POINTER(ServerStats), ctypes.c_int32]),
+    ("lsh_server_destroy", None, [P]),
 ]
 
 
@@ -333,6 +354,66 @@ class Index:
     def close(self):
         if getattr(self, "handle", None):
             lib().lsh_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving loop over an index built with keep_data
+    (lsh_server_* of include/lsh.h).  submit() takes host queries (numpy array
+    or CPU tensor [q, d] of float32 / float16 / bfloat16) and returns a ticket;
+    wait() returns (ids [q, k], dist [q, k], latency_ms) as numpy arrays."""
+
+    def __init__(self, index: Index, max_batch=4096, slots=4, k=10, use_graphs=True, mem_budget=0):
+        cfg = ServerConfig(max_batch, slots, k, int(bool(use_graphs)), int(mem_budget))
+        h = ctypes.c_void_p()
+        _check(lib().lsh_server_create(index.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle, self.index, self.k = h, index, k
+
+    def submit(self, Q) -> int:
+        import numpy as np
+        if isinstance(Q, torch.Tensor):
+            t = Q.detach().contiguous().cpu()
+            dt = _TORCH_DTYPE[t.dtype]
+            q = t.shape[0]
+            ptr = ctypes.c_void_p(t.data_ptr())
+            keep = t
+        else:
+            a = np.ascontiguousarray(Q)
+            dt = {np.dtype(np.float32): F32, np.dtype(np.float16): F16}[a.dtype]
+            q = a.shape[0]
+            ptr = ctypes.c_void_p(a.ctypes.data)
+            keep = a
+        tk = ctypes.c_int64()
+        _check(lib().lsh_server_submit(self.handle, ptr, dt, q, ctypes.byref(tk)))
+        del keep
+        self._q = getattr(self, "_q", {})
+        self._q[int(tk.value)] = q
+        return int(tk.value)
+
+    def wait(self, ticket: int):
+        import numpy as np
+        q = self._q.pop(ticket)
+        ids = np.empty((q, self.k), np.int32)
+        dist = np.empty((q, self.k), np.float32)
+        lat = ctypes.c_double()
+        _check(lib().lsh_server_wait(self.handle, ticket, ctypes.c_void_p(ids.ctypes.data),
+                                     ctypes.c_void_p(dist.ctypes.data), ctypes.byref(lat)))
+        return ids, dist, float(lat.value)
+
+    def stats(self, reset=False):
+        st = ServerStats()
+        _check(lib().lsh_server_stats_get(self.handle, ctypes.byref(st), int(bool(reset))))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().lsh_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
