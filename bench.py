@@ -297,6 +297,74 @@ def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
     return out
 
 
+def serving_bench(dev, e0, e1, stream, max_requests=300):
+    """Serving workload: 10,000,000 x 128 FP16 points from a 1,024-component
+    mixture resident on the GPU; HCS-E2LSH (8 x 16 -> 4 x 4, m = 16) and
+    CS-E2LSH (m = 12), L = 32, each with w the smallest value on a grid that
+    reaches recall@10 >= 0.9 against exact k-NN on 200 noisy queries; Poisson
+    arrivals of log-uniform 1..4096-query batches at 25/50/90% of the measured
+    saturation throughput through the continuous-batching loop."""
+    import numpy as np
+    import torch
+    from paper_2503_06737_gb300 import lsh, measure, workloads
+    wl = workloads.WORKLOADS["gmm1024_10M_d128_f16"]
+    X = workloads.gmm(wl["n"], wl["d"], wl["components"], seed=1237, device=dev, dtype=torch.float16)
+    Qpool, _ = workloads.noisy_queries(X, 20000, wl["query_sigma"], seed=7)
+    Qt = Qpool[:200].contiguous()
+    truth, _ = measure.exact_knn(X, Qt, 10)
+    truth = truth.cpu().numpy()
+    rng = np.random.default_rng(11)
+    out = {"n": wl["n"], "d": wl["d"], "L": wl["L"], "queries": "database rows + N(0, 0.05^2) noise",
+           "batch_sizes": "floor(exp(U[0, ln 4097)))"}
+    for kind, m, dims, mdims in (("hcs_e2lsh", wl["m_hcs"], wl["hcs_dims"], wl["hcs_mdims"]),
+                                 ("cs_e2lsh", wl["m_cs"], None, None)):
+        chosen = None
+        tried = []
+        for w in (2.0, 4.0, 8.0, 16.0, 24.0, 32.0, 48.0, 64.0, 96.0, 128.0):
+            fam = lsh.Family(kind, wl["d"], m, wl["L"], w=w, seed=42, dims=dims, mdims=mdims)
+            idx = fam.build_index(X, keep_data=True)
+            res = idx.query(Qt, k=10, stats=True)
+            rec = measure.recall_at_k(res["ids"].cpu().numpy(), truth)
+            tried.append({"w": w, "recall10": rec, "cand_per_query": res["stats"]["n_unique"] / 200.0})
+            if rec >= 0.9:
+                chosen = (w, fam, idx, rec, res["stats"])
+                break
+            idx.close()
+            fam.close()
+        entry = {"w_grid": tried}
+        if chosen is None:
+            out[kind] = entry
+            continue
+        w, fam, idx, rec, qst = chosen
+        mtx = lsh.dense_matrix(X)
+        e0.record(stream)
+        idx.rebuild_into(mtx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        entry.update({"w": w, "recall10": rec, "m": m, "cand_per_query": qst["n_unique"] / 200.0,
+                      "build_ms": e0.elapsed_time(e1)})
+        srv = lsh.Server(idx, max_batch=4096, slots=4, k=10, use_graphs=True)
+        measure.run_load(srv, Qpool, measure.log_uniform_sizes(40, 4096, rng), None, rng)  # capture graphs
+        sat, lat = measure.run_load(srv, Qpool, measure.log_uniform_sizes(max_requests, 4096, rng), None, rng)
+        entry["saturation_qps"] = sat
+        loads = []
+        for frac in (0.25, 0.5, 0.9):
+            srv.stats(reset=True)
+            qps, lat = measure.run_load(srv, Qpool, measure.log_uniform_sizes(max_requests, 4096, rng),
+                                        frac * sat, rng)
+            loads.append({"offered_qps": frac * sat, "achieved_qps": qps, "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)), "requests": int(len(lat)),
+                          "admitted_peak": srv.stats()["admitted_peak"]})
+        entry["loads"] = loads
+        srv.close()
+        idx.close()
+        fam.close()
+        out[kind] = entry
+    del X, Qpool
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,6 +375,7 @@ def main():
     ap.add_argument("--kind", default="cs_e2lsh")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-family hashing lines")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -330,6 +399,7 @@ def main():
     wl, fam_args = _workload(args.workload, args.kind)
     n, d, L, m = wl["n"], wl["d"], fam_args["L"], fam_args["m"]
     X = _make_X(wl, seed=1235 + rank, device=dev)
+    x_gb = X.numel() * X.element_size() / 1e9
     fam = lsh.Family(**fam_args)
     idx = fam.build_index(X, keep_data=False)
     mtx = lsh.dense_matrix(X)
@@ -452,6 +522,12 @@ def main():
                               "changed": st["n_changed"]}
             f2.close()
         variants.update(extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream))
+    if not args.no_serving and world == 1:
+        idx.close()
+        fam.close()
+        del X, keys, mtx
+        torch.cuda.empty_cache()
+        variants["serving_gmm1024_10M_d128_f16"] = serving_bench(dev, e0, e1, stream)
     clocks.stop()
     clk = clocks.summary(t_wall0, t_wall2)
 
@@ -469,7 +545,7 @@ def main():
             "config": {"workload": args.workload, "kind": fam_args["kind"], "n_per_gpu": n, "d": d,
                        "m": m, "L": L, "w": fam_args["w"],
                        "step": "lsh_index_rebuild: hash (FP32 + FP64 recheck) + radix sort + buckets",
-                       "l2": "inputs larger than L2 (%.2f GB per GPU)" % (X.numel() * X.element_size() / 1e9)},
+                       "l2": "inputs larger than L2 (%.2f GB per GPU)" % x_gb},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "variants": variants,
