@@ -100,7 +100,7 @@ def _declare(L):
     L.orc_family_tables.restype = None
     L.orc_family_tables.argtypes = [U64, I32, I32, P, P, D, P, P, P, P, P]
     L.orc_dense_family.restype = None
-    L.orc_dense_family.argtypes = [U64, I32, I32, I32, D, P, P, P, P]
+    L.orc_dense_family.argtypes = [U64, I32, I32, I32, D, I32, P, P, P, P]
     for nm in ("orc_from_bf16", "orc_from_f16"):
         getattr(L, nm).restype = D
         getattr(L, nm).argtypes = [ctypes.c_uint16]
@@ -190,9 +190,10 @@ class Family:
         return f
 
 
-def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None) -> Family:
+def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32) -> Family:
     """Draw the family (Definitions 2-5) from `seed`.  CS kinds take dims=[d],
-    mdims=[m]; HCS kinds take the mode sizes (prod(dims) >= d, prod(mdims) = m)."""
+    mdims=[m]; HCS kinds take the mode sizes (prod(dims) >= d, prod(mdims) = m).
+    Dense kinds: compute = BF16 rounds every Gaussian entry to bfloat16."""
     kind = KIND_NAMES.get(kind, kind)
     lb = lib()
     if is_dense(kind):
@@ -200,7 +201,7 @@ def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None) -> Family:
         b = np.empty((L, m), np.float64)
         ka = np.empty((L, m), np.uint32)
         kb = np.empty((L, m), np.uint32)
-        lb.orc_dense_family(seed, L, d, m, w, _p(G), _p(b), _p(ka), _p(kb))
+        lb.orc_dense_family(seed, L, d, m, w, int(compute), _p(G), _p(b), _p(ka), _p(kb))
         return Family(kind, d, m, L, float(w), seed, [d], [m], G=G, b=b, ka=ka, kb=kb)
     if kind in (CS_E2LSH, CS_SRP):
         dims, mdims = [d], [m]

@@ -118,17 +118,30 @@ void orc_family_tables(uint64_t seed, int L, int N, const int32_t *dims,
   }
 }
 
+/* Round a finite binary32 value to the nearest bfloat16 (8-bit significand),
+ * ties to even, and return it as binary32. */
+static float orc_round_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  uint32_t lower = u & 0xFFFFu, keep = u & 0xFFFF0000u;
+  uint32_t half = 0x8000u;
+  if (lower > half || (lower == half && (keep & 0x10000u))) keep += 0x10000u;
+  memcpy(&f, &keep, 4);
+  return f;
+}
+
 /*
  * Dense Gaussian projection family (Definitions 2 and 3: r ~ N(0, I_d)).
  * Per table t: for j = 0..d-1, for l = 0..m-1: two draws r1, r2;
  *   u1 = (hi53(r1) + 1) 2^-53 in (0,1], u2 = hi53(r2) 2^-53 in [0,1);
  *   g = sqrt(-2 ln u1) cos(2 pi u2)                          (Box-Muller);
- *   G[j][t*m + l] = g rounded to FP32;
+ *   G[j][t*m + l] = g rounded to FP32 (compute = 0), or that FP32 value rounded
+ *   to bfloat16 (compute = 1);
  * then b and ka/kb exactly as in orc_family_tables.
  * G is [d][m*L] row-major.
  */
-void orc_dense_family(uint64_t seed, int L, int d, int m, double w, float *G,
-                      double *b, uint32_t *ka, uint32_t *kb) {
+void orc_dense_family(uint64_t seed, int L, int d, int m, double w, int compute,
+                      float *G, double *b, uint32_t *ka, uint32_t *kb) {
   const double two_pi = 6.283185307179586;
   const int64_t ldg = (int64_t)m * L;
   for (int t = 0; t < L; ++t) {
@@ -140,7 +153,8 @@ void orc_dense_family(uint64_t seed, int L, int d, int m, double w, float *G,
         double u1 = (double)((r1 >> 11) + 1) * 0x1.0p-53;
         double u2 = (double)(r2 >> 11) * 0x1.0p-53;
         double g = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
-        G[(int64_t)j * ldg + (int64_t)t * m + l] = (float)g;
+        float g32 = (float)g;
+        G[(int64_t)j * ldg + (int64_t)t * m + l] = compute == 1 ? orc_round_bf16(g32) : g32;
       }
     }
     for (int l = 0; l < m; ++l) {

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 
@@ -34,6 +35,16 @@ class Stream {
 };
 
 inline double unit53(uint64_t r) { return double(r >> 11) * 0x1.0p-53; }
+
+// Round a finite FP32 value to the nearest bfloat16 (ties to even), widened back.
+inline float to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
 
 void draw_offsets_and_keys(Stream &s, const lsh_family_desc &d, int t, HostFamily &hf) {
   const int m = d.m;
@@ -67,7 +78,8 @@ void sample_family(const lsh_family_desc &d, HostFamily &hf) {
           const double u2 = double(r2 >> 11) * 0x1.0p-53;        // [0, 1)
           const double radius = std::sqrt(-2.0 * std::log(u1));
           const double g = radius * std::cos(two_pi * u2);
-          hf.G[size_t(j) * ldg + size_t(t) * m + l] = float(g);
+          const float g32 = float(g);
+          hf.G[size_t(j) * ldg + size_t(t) * m + l] = d.compute == LSH_BF16 ? to_bf16(g32) : g32;
         }
       draw_offsets_and_keys(s, d, t, hf);
     }

@@ -29,7 +29,7 @@ lsh_status cuda_fail(cudaError_t e, const char *what);
 void count_launches(uint64_t k);
 
 // Sticky device status bits (family status word).
-enum : uint32_t { STATUS_NONFINITE = 1u, STATUS_OVERFLOW = 2u };
+enum : uint32_t { STATUS_NONFINITE = 1u, STATUS_OVERFLOW = 2u, STATUS_TIMEOUT = 4u };
 
 // Per-call device counters (order matches lsh_hash_stats after n_entries).
 enum { CNT_FLAGGED = 0, CNT_CHANGED = 1, CNT_NONFINITE = 2, CNT_OVERFLOW = 3, CNT_NUM = 8 };
@@ -81,6 +81,8 @@ struct lsh_family_s {
   float *d_G = nullptr;           // [d][m*L] dense kinds
   float *d_Gt = nullptr;          // [m*L][d] transposed copy (FP64 recheck reads columns)
   float *d_gnorm = nullptr;       // [m*L] column norms, rounded up
+  uint16_t *d_Gt16 = nullptr;     // [m*L][d] bf16 bits (families with BF16 G)
+  float *d_gnc = nullptr;         // [m*L][4] column norms per K chunk of the tensor-core path
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
@@ -153,6 +155,13 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
 // keys and multi-word SRP bits must be zeroed by the caller.
 cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float *Gt, const float *gnorm,
                               cudaStream_t stream);
+
+// Dense E2LSH / SRP on the tensor cores (TMA + tcgen05, BF16 x BF16 -> FP32),
+// for BF16 rows and a family whose G is stored in BF16.  xnc_scratch: [n][4] floats.
+bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X);
+int tc_chunk_ktiles(int d);
+cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
+                            float *xnc_scratch, cudaStream_t stream);
 
 // Query path: probe + dedup + exact top-k rerank, one CTA per query.
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,

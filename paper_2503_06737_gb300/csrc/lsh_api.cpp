@@ -2,6 +2,7 @@
 // ownership, per-call temporaries and error reporting around the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -38,7 +39,8 @@ lsh_status validate_desc(const lsh_family_desc &d) {
   if (d.L < 1) return fail(LSH_EINVAL, "L must be >= 1");
   if (!(d.w > 0.0) || !std::isfinite(d.w)) return fail(LSH_EINVAL, "w must be finite and > 0");
   if (kind_is_dense(d.kind)) {
-    if (d.compute != LSH_F32) return fail(LSH_EUNSUPPORTED, "dense families store G in FP32 in this build");
+    if (d.compute != LSH_F32 && d.compute != LSH_BF16)
+      return fail(LSH_EUNSUPPORTED, "dense families store G in FP32 or BF16");
     if (int64_t(d.d) * d.m * d.L > (int64_t(1) << 31)) return fail(LSH_EINVAL, "G too large");
     return LSH_OK;
   }
@@ -78,6 +80,8 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_G);
   cudaFree(f->d_Gt);
   cudaFree(f->d_gnorm);
+  cudaFree(f->d_Gt16);
+  cudaFree(f->d_gnc);
   cudaFree(f->d_status);
   cudaFree(f->d_colmajor);
   delete f;
@@ -147,6 +151,15 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.proj = proj;
   p.counters = counters;
   p.status = f->d_status;
+  if (kind_is_dense(d.kind) && f->d_Gt16 && tc_dense_supported(d, X)) {
+    float *xnc = nullptr;
+    LSH_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&xnc), sizeof(float) * 4 * size_t(X->n), stream));
+    const cudaError_t e = launch_tc_dense(p, f->d_Gt16, f->d_Gt, f->d_gnc, xnc, stream);
+    cudaFreeAsync(xnc, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core dense hash");
+    count_launches(2);
+    return LSH_OK;
+  }
   if (kind_is_dense(d.kind)) {
     if (keys) LSH_CUDA_TRY(cudaMemsetAsync(keys, 0, sizeof(uint64_t) * size_t(key_ld) * d.L, stream));
     if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
@@ -275,6 +288,25 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
     }
     if (e == cudaSuccess) e = upload(&f->d_Gt, gt.data(), gt.size());
     if (e == cudaSuccess) e = upload(&f->d_gnorm, gn.data(), gn.size());
+    if (e == cudaSuccess && d.compute == LSH_BF16) {
+      // bf16 copy of G^T for the tensor cores, and its column norms per K chunk
+      std::vector<uint16_t> g16(gt.size());
+      for (size_t i = 0; i < gt.size(); ++i) {
+        uint32_t u;
+        std::memcpy(&u, &gt[i], 4);
+        g16[i] = uint16_t(u >> 16);  // exact: the entries are bf16 values
+      }
+      const int clen = tc_chunk_ktiles(d.d) * 64;
+      std::vector<float> gnc(ml * 4, 0.f);
+      for (size_t c = 0; c < ml; ++c)
+        for (int k = 0; k < 4; ++k) {
+          double s2 = 0.0;
+          for (int j = k * clen; j < std::min(d.d, (k + 1) * clen); ++j) s2 += double(gt[c * d.d + j]) * gt[c * d.d + j];
+          gnc[c * 4 + k] = float(std::sqrt(s2) * (1.0 + 1e-6));
+        }
+      e = upload(&f->d_Gt16, g16.data(), g16.size());
+      if (e == cudaSuccess) e = upload(&f->d_gnc, gnc.data(), gnc.size());
+    }
   }
   if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {
     // column-major copy of the count-sketch tables for the CSR kernel

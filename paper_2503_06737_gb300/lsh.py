@@ -190,10 +190,10 @@ def make_desc(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32)
     return desc
 
 
-def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None):
+def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32):
     """The library's host sampler alone (no device): dict of numpy tables."""
     import numpy as np
-    desc = make_desc(kind, d, m, L, w, seed, dims, mdims)
+    desc = make_desc(kind, d, m, L, w, seed, dims, mdims, compute)
     dense = desc.kind in (E2LSH, SRP)
     dsum = 0 if dense else sum(desc.dims[k] for k in range(desc.N))
     bins = np.empty((L, dsum), np.int32)

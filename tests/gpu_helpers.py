@@ -44,7 +44,8 @@ def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
     Xh, dt = to_oracle(Xs)
     ofam = oracle.family(fam_args["kind"], fam_args["d"], fam_args["m"], fam_args["L"],
                          w=fam_args.get("w", 4.0), seed=fam_args.get("seed", 42),
-                         dims=fam_args.get("dims"), mdims=fam_args.get("mdims"))
+                         dims=fam_args.get("dims"), mdims=fam_args.get("mdims"),
+                         compute=fam_args.get("compute", 0))
     st, y, codes, keys = oracle.hash_dense(ofam, Xh, dtype=dt)
     assert st == 0
     m = fam_args["m"]

@@ -88,3 +88,15 @@ def test_null_arguments(L):
     assert lib.lsh_index_export(None, None, None, None, None) == 1
     lib.lsh_family_destroy(None)
     lib.lsh_index_destroy(None)
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+def test_bf16_family_matches_oracle(L, orc, kind):
+    import torch
+    a = L.sample_family_tables(kind, 512, 32, 4, seed=77, compute=1)
+    f = orc.family(kind, 512, 32, 4, seed=77, compute=1)
+    assert np.array_equal(a["G"], f.G)
+    # the entries are the FP32 draws rounded to bfloat16 (ties to even), as torch rounds them
+    g32 = orc.family(kind, 512, 32, 4, seed=77).G
+    want = torch.from_numpy(g32).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(f.G, want)

@@ -54,3 +54,23 @@ def test_dense_index_and_query():
     Q, _ = workloads.noisy_queries(X, 20, 0.05, seed=9)
     _run(dict(kind="e2lsh", d=64, m=8, L=6, w=4.0, seed=5), X, Q, k=10)
     _run(dict(kind="srp", d=64, m=8, L=6, seed=5), X, Q, k=10)
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 960, 64, 2), (77, 64, 8, 32)])
+def test_dense_bf16_tensor_core_parity(kind, n, d, m, L):
+    """BF16 rows and a BF16 family: the tcgen05 path (TMA, TMEM K-chunk
+    accumulators, fused epilogue) against the oracle, bit-exact."""
+    X = workloads.iid(n, d, seed=n + d, device="cpu", dtype=torch.bfloat16).cuda()
+    args = dict(kind=kind, d=d, m=m, L=L, w=4.0, seed=31, compute=1)
+    stats, rel = compare_hash(args, X)
+    assert stats["n_changed"] <= stats["n_flagged"]
+
+
+def test_dense_bf16_tensor_core_equals_simt_path():
+    # strided rows (ld = 520, not a multiple of 8) take the SIMT path; both are exact
+    X = workloads.iid(256, 520, seed=5, device="cpu", dtype=torch.bfloat16).cuda()
+    fam = lsh.Family("e2lsh", 512, 32, 8, w=4.0, seed=3, compute=1)
+    a = fam.hash(X[:, :512].contiguous(), codes=True, keys=True)
+    b = fam.hash(X[:, :512], codes=True, keys=True)
+    assert torch.equal(a["codes"], b["codes"]) and torch.equal(a["keys"], b["keys"])
