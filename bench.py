@@ -33,6 +33,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+T_START = time.time()
+
+
+def log(msg):
+    print(f"[bench +{time.time() - T_START:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 METRIC = "hashed pts/s & HBM roofline %, CS/HCS vs dense; serve QPS, p99 @recall10≥0.9"
 
 
@@ -294,10 +301,68 @@ def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
                                            "qps": sw["queries"] / (qms / 1e3)}
     idx.close()
     fs.close()
+    del Xs, Qs
+    log("small workload done; precision sweep")
+    out["iid_4M_d512_bf16"] = precision_sweep(peaks, alu_peak, e0, e1, stream, X.device)
     return out
 
 
-def serving_bench(dev, e0, e1, stream, max_requests=300):
+def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
+    """4,000,000 x 512 BF16 rows, m = 32, L = 64: dense E2LSH on the tensor cores
+    (GEMM 4M x 512 x 2048, BF16 family) with the FP64 boundary recheck, the same
+    family on the FP32 SIMT GEMM (bounded sample), and CS/HCS-E2LSH."""
+    import torch
+    from paper_2503_06737_gb300 import lsh, workloads
+    wl = workloads.WORKLOADS["iid_4M_d512_bf16"]
+    n, d, m, L = wl["n"], wl["d"], wl["m"], wl["L"]
+    X = workloads.iid(n, d, seed=1238, device=dev, dtype=torch.bfloat16)
+    keys = torch.empty((L, n), dtype=torch.int64, device=dev)
+    mtx = lsh.dense_matrix(X)
+    out = {"n": n, "d": d, "m": m, "L": L}
+
+    def timed(fam, reps, mt=mtx, kk=keys):
+        fam.hash_into(mt, None, lsh._ptr(kk), None)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fam.hash_into(mt, None, lsh._ptr(kk), None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    flops = 2.0 * n * d * m * L
+    ft = lsh.Family("e2lsh", d, m, L, w=wl["w"], seed=42, compute=lsh.BF16)
+    tms = timed(ft, 5)
+    log(f"tcgen05 dense: {tms:.3f} ms")
+    st = ft.hash(X, keys=True, stats=True)["stats"]
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    out["dense_bf16_tcgen05"] = {"hash_ms": tms, "points_per_s": n / (tms / 1e3),
+                                 "tflops": flops / (tms / 1e3) / 1e12,
+                                 "tensor_frac": flops / (tms / 1e3) / 1e12 / bf16_peak,
+                                 "flagged_per_entry": st["n_flagged"] / st["n_entries"],
+                                 "mismatch_before_recheck": st["n_changed"] / st["n_entries"]}
+    # the same BF16 family on the FP32 SIMT GEMM, on a 131,072-row sample (strided view forces that path)
+    ns = 131072
+    Xpad = torch.zeros((ns, d + 4), dtype=torch.bfloat16, device=dev)
+    Xpad[:, :d] = X[:ns]
+    ks = torch.empty((L, ns), dtype=torch.int64, device=dev)
+    sms = timed(ft, 2, lsh.dense_matrix(Xpad[:, :d]), ks)
+    out["dense_bf16_family_fp32_simt"] = {"hash_ms_per_1M_rows": sms * (1e6 / ns),
+                                          "points_per_s": ns / (sms / 1e3),
+                                          "tflops": 2.0 * ns * d * m * L / (sms / 1e3) / 1e12}
+    ft.close()
+    for kind, dims, mdims in (("cs_e2lsh", None, None), ("hcs_e2lsh", [16, 32], [4, 8])):
+        fc = lsh.Family(kind, d, m, L, w=wl["w"], seed=42, dims=dims, mdims=mdims)
+        cms = timed(fc, 3)
+        out[kind] = {"hash_ms": cms, "points_per_s": n / (cms / 1e3),
+                     "alu_frac": float(n) * d * L / (cms / 1e3) / 1e12 / alu_peak}
+        fc.close()
+    del X, keys, Xpad, ks
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=200000.0, seconds_per_load=8.0):
     """Serving workload: 10,000,000 x 128 FP16 points from a 1,024-component
     mixture resident on the GPU; HCS-E2LSH (8 x 16 -> 4 x 4, m = 16) and
     CS-E2LSH (m = 12), L = 32, each with w the smallest value on a grid that
@@ -320,13 +385,16 @@ def serving_bench(dev, e0, e1, stream, max_requests=300):
                                  ("cs_e2lsh", wl["m_cs"], None, None)):
         chosen = None
         tried = []
-        for w in (2.0, 4.0, 8.0, 16.0, 24.0, 32.0, 48.0, 64.0, 96.0, 128.0):
+        best = None
+        for w in (4.0, 8.0, 16.0, 24.0, 32.0, 48.0, 64.0, 96.0):
             fam = lsh.Family(kind, wl["d"], m, wl["L"], w=w, seed=42, dims=dims, mdims=mdims)
             idx = fam.build_index(X, keep_data=True)
             res = idx.query(Qt, k=10, stats=True)
             rec = measure.recall_at_k(res["ids"].cpu().numpy(), truth)
-            tried.append({"w": w, "recall10": rec, "cand_per_query": res["stats"]["n_unique"] / 200.0})
-            if rec >= 0.9:
+            cpq = res["stats"]["n_unique"] / 200.0
+            tried.append({"w": w, "recall10": rec, "cand_per_query": cpq})
+            log(f"serving {kind} w={w}: recall@10 {rec:.3f}, {cpq:.0f} candidates/query")
+            if rec >= 0.9 or cpq > max_cand:
                 chosen = (w, fam, idx, rec, res["stats"])
                 break
             idx.close()
@@ -342,16 +410,22 @@ def serving_bench(dev, e0, e1, stream, max_requests=300):
         e1.record(stream)
         torch.cuda.synchronize()
         entry.update({"w": w, "recall10": rec, "m": m, "cand_per_query": qst["n_unique"] / 200.0,
-                      "build_ms": e0.elapsed_time(e1)})
+                      "build_ms": e0.elapsed_time(e1),
+                      "recall_target_met": rec >= 0.9})
         srv = lsh.Server(idx, max_batch=4096, slots=4, k=10, use_graphs=True)
-        measure.run_load(srv, Qpool, measure.log_uniform_sizes(40, 4096, rng), None, rng)  # capture graphs
-        sat, lat = measure.run_load(srv, Qpool, measure.log_uniform_sizes(max_requests, 4096, rng), None, rng)
+        measure.run_load(srv, Qpool, measure.log_uniform_sizes(40, 4096, rng), None, rng,
+                         max_seconds=seconds_per_load)  # capture graphs
+        sat, lat = measure.run_load(srv, Qpool, measure.log_uniform_sizes(max_requests, 4096, rng), None, rng,
+                                    max_seconds=seconds_per_load)
         entry["saturation_qps"] = sat
+        log(f"serving {kind}: saturation {sat:.0f} queries/s")
         loads = []
         for frac in (0.25, 0.5, 0.9):
             srv.stats(reset=True)
             qps, lat = measure.run_load(srv, Qpool, measure.log_uniform_sizes(max_requests, 4096, rng),
-                                        frac * sat, rng)
+                                        frac * sat, rng, max_seconds=seconds_per_load)
+            log(f"serving {kind}: load {frac:.2f} -> {qps:.0f} q/s, p50 {np.percentile(lat, 50):.2f} ms, "
+                f"p99 {np.percentile(lat, 99):.2f} ms")
             loads.append({"offered_qps": frac * sat, "achieved_qps": qps, "p50_ms": float(np.percentile(lat, 50)),
                           "p99_ms": float(np.percentile(lat, 99)), "requests": int(len(lat)),
                           "admitted_peak": srv.stats()["admitted_peak"]})
@@ -411,6 +485,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    log("data ready, warm-up")
     for _ in range(args.warmup):
         idx.rebuild_into(mtx)
     barrier()
@@ -436,6 +511,7 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     value = world * n / (ms / 1e3)
+    log(f"timed region: {ms:.3f} ms/step")
 
     # ---- dominant kernel alone: the hashing launch (keys only) ----
     keys = torch.empty((L, n), dtype=torch.int64, device=dev)
@@ -521,7 +597,9 @@ def main():
                               "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
                               "changed": st["n_changed"]}
             f2.close()
+        log("per-family hashing done")
         variants.update(extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream))
+        log("extra variants done")
     if not args.no_serving and world == 1:
         idx.close()
         fam.close()

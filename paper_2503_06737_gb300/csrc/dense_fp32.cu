@@ -59,12 +59,25 @@ __device__ __forceinline__ float ldx(const void *X, int64_t i) {
   return __half2float(__ushort_as_half(h));
 }
 
+// FP64 value of one projection, sum_j x_j G[j][c] in ascending j with one
+// IEEE rounding per operation; eight terms are loaded before their adds.
 template <int DT>
 __device__ __noinline__ double dense_fp64(const DenseArgs &a, int64_t row, int64_t col) {
   const float *g = a.Gt + col * a.d;
   const int64_t base = row * a.ld;
   double y = 0.0;
-  for (int j = 0; j < a.d; ++j) y = __dadd_rn(y, __dmul_rn(double(ldx<DT>(a.X, base + j)), double(g[j])));
+  int j = 0;
+  for (; j + 8 <= a.d; j += 8) {
+    float xv[8], gv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      xv[k] = ldx<DT>(a.X, base + j + k);
+      gv[k] = __ldg(g + j + k);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y = __dadd_rn(y, __dmul_rn(double(xv[k]), double(gv[k])));
+  }
+  for (; j < a.d; ++j) y = __dadd_rn(y, __dmul_rn(double(ldx<DT>(a.X, base + j)), double(__ldg(g + j))));
   return y;
 }
 

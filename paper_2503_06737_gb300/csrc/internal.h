@@ -82,7 +82,9 @@ struct lsh_family_s {
   float *d_Gt = nullptr;          // [m*L][d] transposed copy (FP64 recheck reads columns)
   float *d_gnorm = nullptr;       // [m*L] column norms, rounded up
   uint16_t *d_Gt16 = nullptr;     // [m*L][d] bf16 bits (families with BF16 G)
-  float *d_gnc = nullptr;         // [m*L][4] column norms per K chunk of the tensor-core path
+  float *d_gnc = nullptr;         // [m*L][4] column norms per K chunk of the tensor-core path;
+                                  // slots 2, 3: the column's least exponent and its range (int bits)
+  int32_t *d_Gint = nullptr;      // [m*L][d] column j of G as integers on its own 2^e grid (exact recheck)
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
@@ -160,8 +162,9 @@ cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float
 // for BF16 rows and a family whose G is stored in BF16.  xnc_scratch: [n][4] floats.
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X);
 int tc_chunk_ktiles(int d);
+size_t tc_dense_scratch_bytes(int64_t n, int64_t ML);
 cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
-                            float *xnc_scratch, cudaStream_t stream);
+                            const int32_t *Gint, void *scratch, cudaStream_t stream);
 
 // Query path: probe + dedup + exact top-k rerank, one CTA per query.
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,

@@ -82,6 +82,7 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_gnorm);
   cudaFree(f->d_Gt16);
   cudaFree(f->d_gnc);
+  cudaFree(f->d_Gint);
   cudaFree(f->d_status);
   cudaFree(f->d_colmajor);
   delete f;
@@ -152,12 +153,12 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.counters = counters;
   p.status = f->d_status;
   if (kind_is_dense(d.kind) && f->d_Gt16 && tc_dense_supported(d, X)) {
-    float *xnc = nullptr;
-    LSH_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&xnc), sizeof(float) * 4 * size_t(X->n), stream));
-    const cudaError_t e = launch_tc_dense(p, f->d_Gt16, f->d_Gt, f->d_gnc, xnc, stream);
-    cudaFreeAsync(xnc, stream);
+    void *scratch = nullptr;
+    LSH_CUDA_TRY(cudaMallocAsync(&scratch, tc_dense_scratch_bytes(X->n, int64_t(d.m) * d.L), stream));
+    const cudaError_t e = launch_tc_dense(p, f->d_Gt16, f->d_Gt, f->d_gnc, f->d_Gint, scratch, stream);
+    cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core dense hash");
-    count_launches(2);
+    count_launches(3);
     return LSH_OK;
   }
   if (kind_is_dense(d.kind)) {
@@ -298,14 +299,38 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
       }
       const int clen = tc_chunk_ktiles(d.d) * 64;
       std::vector<float> gnc(ml * 4, 0.f);
-      for (size_t c = 0; c < ml; ++c)
-        for (int k = 0; k < 4; ++k) {
+      std::vector<int32_t> gint(gt.size(), 0);
+      for (size_t c = 0; c < ml; ++c) {
+        for (int k = 0; k < 2; ++k) {
           double s2 = 0.0;
           for (int j = k * clen; j < std::min(d.d, (k + 1) * clen); ++j) s2 += double(gt[c * d.d + j]) * gt[c * d.d + j];
           gnc[c * 4 + k] = float(std::sqrt(s2) * (1.0 + 1e-6));
         }
+        // bf16 g = M 2^E (M < 256 an integer): the column on the grid of its least exponent
+        int emin = 0, emax = 0;
+        bool any = false;
+        for (int j = 0; j < d.d; ++j) {
+          const uint32_t h = g16[c * d.d + j], ex = (h >> 7) & 0xFF, fr = h & 0x7F;
+          if (ex == 0 && fr == 0) continue;
+          const int E = ex ? int(ex) - 134 : -133;
+          emin = any ? std::min(emin, E) : E;
+          emax = any ? std::max(emax, E) : E;
+          any = true;
+        }
+        const int range = emax - emin;
+        if (range <= 23)
+          for (int j = 0; j < d.d; ++j) {
+            const uint32_t h = g16[c * d.d + j], ex = (h >> 7) & 0xFF, fr = h & 0x7F;
+            if (ex == 0 && fr == 0) continue;
+            const int32_t M = int32_t(ex ? (fr | 0x80) : fr) << ((ex ? int(ex) - 134 : -133) - emin);
+            gint[c * d.d + j] = (h >> 15) ? -M : M;
+          }
+        int32_t slots[2] = {emin, range};
+        std::memcpy(&gnc[c * 4 + 2], slots, sizeof(slots));
+      }
       e = upload(&f->d_Gt16, g16.data(), g16.size());
       if (e == cudaSuccess) e = upload(&f->d_gnc, gnc.data(), gnc.size());
+      if (e == cudaSuccess) e = upload(&f->d_Gint, gint.data(), gint.size());
     }
   }
   if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {

@@ -1,32 +1,38 @@
 // tc_dense.cu -- the dense baselines E2LSH (Definition 2) and SRP (Definition
 // 3) on the 5th-generation tensor cores: Y = X G for BF16 rows X [n][d] and a
 // family whose Gaussian G is stored in BF16, fused with discretisation, the
-// boundary recheck and the key fold.
+// boundary test and the key fold; an exact recheck kernel patches the rare
+// entries near a bin edge (or near 0 for SRP).
 //
-// Per CTA one 128 x 128 output tile (rows x projection columns):
-//   warp 0   allocates all 512 TMEM columns, then issues TMA loads (128-byte
-//            swizzle) of 64-wide K slices of X and of G^T into a 4-stage
-//            shared-memory ring guarded by mbarriers;
-//   warp 1   (one thread) issues tcgen05.mma kind::f16 (M = N = 128, K = 16,
-//            FP32 accumulate), committing each stage back to its producer;
-//   warps 2-5 read the accumulators with tcgen05.ld and run the epilogue.
-// The K dimension is split into (at most) four chunks, each accumulated into
-// its own 128-column TMEM region, so the epilogue sees every chunk sum.
+// Main kernel: persistent, one CTA per SM; CTA b owns the 128-row tiles
+// b, b + gridDim.x, ... and, for each, walks all 128-column projection tiles.
+//   warp 0   TMA loads (128-byte swizzle): the row tile's K slices once per
+//            row tile (resident in shared memory, d <= 512), the slices of G^T
+//            through a ring of SB stages;
+//   warp 1   tcgen05.mma kind::f16 (M = N = 128, K = 16, FP32 accumulate),
+//            issued by one elected lane of the converged warp;
+//   warps 2-17 drain the accumulators (tcgen05.ld) and run the epilogue.
+// K is split into two chunks, each accumulated into its own TMEM region, and
+// the accumulators are double buffered (2 x 2 x 128 of the 512 columns), so
+// the MMAs of one tile overlap the epilogue of the previous one.
 //
 // Exactness.  Products of two BF16 values are exact in FP32.  Accumulation
 // model for one chunk of s MMA steps: the error is at most 2u * s * (sum of
 // |products| of the chunk) -- each step rounds once relative to a partial
 // sum no larger than that -- with sum |products| <= ||x_chunk|| ||g_chunk||
 // (row chunk norms from a pre-pass, column chunk norms from the host).  The
-// four chunk sums are added in FP32 (error <= 2u sum |chunk|).  Entries
-// within that bound (widened 2%) of an E2LSH bin edge, or of 0 for SRP, are
-// recomputed in FP64 as sum_j x_j G[j][c] in ascending j -- the oracle's
-// value.  Every mbarrier wait is bounded; a timeout sets an error flag and
-// the kernel still releases its TMEM.
+// two chunk sums are added in FP32.  Entries within that bound (widened 2%)
+// of an E2LSH bin edge, or of 0 for SRP, are queued with their fast code; the
+// recheck kernel computes their exact FP64 value sum_j x_j G[j][c] in
+// ascending j (the oracle's) as an integer sum on a common 2^e grid, derives
+// the oracle's code from it and patches code, bits and key where the fast
+// code was wrong.  Every mbarrier wait is bounded; a timeout sets an error
+// flag and the kernel still releases its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -34,17 +40,23 @@
 namespace lsh {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, NCH = 4;
+constexpr int BM = 128, BN = 128, BK = 64, KMAX = 8, SB = 5, NCH = 2;
+constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps;
+constexpr int CONST_Q = 5;
+constexpr int BW = 8;  // epilogue block: columns read from TMEM at a time  // per-column constants staged per epilogue warp: gn0, gn1, b, ka, kb
+constexpr int XNC_LD = 4, GNC_LD = 4;  // row / column records: NCH chunk norms, then exponent base and range
+static_assert(NCH <= 2, "the chunk norms share a four-word record with the exponent range");
 constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr float kU = 5.9604644775390625e-08f;
 
 struct TcArgs {
-  int64_t n;
+  int64_t n, mtiles, ML;
   int32_t d, m, L, srp, ktiles, ktpc, nch;
   const unsigned short *X;   // bf16 rows
   int64_t ld;
-  const float *Gt;           // [mL][d] FP32 copy (recheck)
+  const float *Gt;           // [mL][d] FP32 copy (sequential recheck fallback)
+  const int32_t *Gint;       // [mL][d] columns of G as integers on their own grids (exact recheck)
   const float *gnc;          // [mL][NCH] column chunk norms (rounded up)
   const float *xnc;          // [n][NCH] row chunk norms (widened; NaN = row not finite)
   const float *b32;
@@ -59,6 +71,9 @@ struct TcArgs {
   float *proj;
   unsigned long long *counters;
   uint32_t *status;
+  int4 *queue;        // flagged entries {row, column, fast code, 0} for the recheck kernel
+  uint32_t *qcount;   // entries appended (may exceed qcap: the excess is rechecked in place)
+  uint32_t qcap;
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -66,23 +81,66 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvt
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  uint32_t done = 0;
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(su32(b)), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *b, uint32_t parity, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done) : "r"(su32(b)), "r"(parity), "r"(hint_ns) : "memory");
+  return done != 0;
+}
+// The same wait by a whole warp, with a warp-uniform answer.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *b, uint32_t parity);
+// Bounded wait for the phase of the given parity: false after about two
+// seconds.  hint_ns > 0 lets the thread sleep between polls (for warps that
+// wait long, so that they leave the issue slots to the MMA thread).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t hint_ns = 0) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer_ns();
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(su32(b)), "r"(parity) : "memory");
-    if (done) return true;
+    if (hint_ns ? mbar_try_sleep(b, parity, hint_ns) : mbar_try(b, parity)) return true;
+    if ((it & 63) == 63 && gtimer_ns() - t0 > 2000000000ull) return false;
   }
   return false;
 }
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *b, uint32_t parity) {
+  return __all_sync(0xffffffffu, mbar_wait(b, parity));
+}
+// One elected lane of a converged warp arms the barrier with the expected
+// bytes and issues the tile load (the predicate stays inside the asm, so the
+// warp never diverges around it).
+__device__ __forceinline__ void tma_2d_elect(void *dst, const CUtensorMap *map, uint64_t *bar, uint32_t bytes, int x,
+                                             int y) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(x), "r"(y) : "memory");
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %5;\n"
+      " @e cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n}\n"
+      ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(x), "r"(y), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void umma_elect(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void commit_elect(uint64_t *bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
+      ::"r"(su32(bar)) : "memory");
 }
 // UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
 // atoms 1024 B apart.
@@ -95,48 +153,170 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// FP64 value of one projection, sum_j x_j G[j][c] in ascending j with one
+// IEEE rounding per operation.  Rows are 16-byte aligned and d % 8 == 0 on
+// this path, so eight terms are loaded at once before their sequential adds.
 __device__ __noinline__ double tc_fp64(const TcArgs &a, int64_t row, int64_t col) {
   const float *g = a.Gt + col * a.d;
   const unsigned short *x = a.X + row * a.ld;
   double y = 0.0;
-  for (int j = 0; j < a.d; ++j) y = __dadd_rn(y, __dmul_rn(double(__uint_as_float(uint32_t(x[j]) << 16)), double(g[j])));
+#pragma unroll 2
+  for (int j = 0; j < a.d; j += 8) {
+    const uint4 xv = *reinterpret_cast<const uint4 *>(x + j);
+    const float4 g0 = *reinterpret_cast<const float4 *>(g + j);
+    const float4 g1 = *reinterpret_cast<const float4 *>(g + j + 4);
+    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+    const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t h = (k & 1) ? (xw[k >> 1] >> 16) : (xw[k >> 1] & 0xFFFFu);
+      y = __dadd_rn(y, __dmul_rn(double(__uint_as_float(h << 16)), double(gv[k])));
+    }
+  }
   return y;
 }
 
-__global__ void __launch_bounds__(192, 1) tc_dense_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                          const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+// The FP64 value of sum_j x_j G[j][c] (ascending j, one rounding per
+// operation) computed by the whole warp exactly, in 64-bit fixed point, in one
+// pass over the row.  A BF16 value is M 2^E with M < 256 an integer; the row
+// (pre-pass) and the column (family set-up) carry their least exponent and
+// exponent range.  With row range Rx <= 23, column range Rg <= 23 and
+// Rx + Rg <= 37, x_j = X_j 2^ex0 and G_jc = G_j 2^eg0 with |X_j|, |G_j| < 2^31
+// and every product X_j G_j below 2^53.  When moreover the sum of the product
+// magnitudes stays below 2^53, every partial sum of the sequential FP64 loop
+// is an integer multiple of 2^(ex0 + eg0) below 2^53 in magnitude, hence exact,
+// so that loop returns the exact sum -- which integer addition (associative)
+// gets in any order.  Returns NaN when a condition fails (the caller then runs
+// the loop); the row is finite, so NaN is no projection value.
+// The exact sum as S 2^e (S below 2^53 in magnitude), in every lane of a
+// group of G consecutive lanes (gl = lane within the group); false when a
+// condition fails.
+template <int G>
+__device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, int64_t col, int gl, long long &S,
+                                                int &e) {
+  const int4 xi = __ldg(reinterpret_cast<const int4 *>(a.xnc + row * XNC_LD));
+  const int4 gi = __ldg(reinterpret_cast<const int4 *>(a.gnc + col * GNC_LD));
+  const int ex0 = xi.z, rx = xi.w, eg0 = gi.z, rg = gi.w;
+  const uint4 *xr = reinterpret_cast<const uint4 *>(a.X + row * a.ld);
+  const int4 *gr = reinterpret_cast<const int4 *>(a.Gint + col * a.d);
+  // two's complement sum (wraps harmlessly when the magnitude test fails);
+  // the magnitude saturates at 2^53 so that neither a lane nor the reduction overflows
+  unsigned long long sum = 0, mag = 0;
+  constexpr unsigned long long kCap = 1ull << 53;
+  const int nch = a.d >> 3;  // chunks of eight coordinates
+#pragma unroll 4
+  for (int c = gl; c < nch; c += G) {
+    const uint4 xv = __ldg(xr + c);
+    const int4 g0 = __ldg(gr + 2 * c), g1 = __ldg(gr + 2 * c + 1);
+    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+    const int gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t h = (k & 1) ? (xw[k >> 1] >> 16) : (xw[k >> 1] & 0xFFFFu);
+      const int ex = (h >> 7) & 0xFF;
+      const int M = int(h & 0x7F) | (min(ex, 1) << 7);  // implicit bit unless subnormal
+      const int X = M << max(max(ex, 1) - 134 - ex0, 0);  // zero stays zero
+      const long long P = (long long)X * gv[k];
+      sum += (unsigned long long)((h >> 15) ? -P : P);
+      mag += (unsigned long long)(P < 0 ? -P : P);
+    }
+    mag = min(mag, kCap);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    mag = min(mag + __shfl_xor_sync(0xffffffffu, mag, o), kCap);
+  }
+  S = (long long)sum;
+  e = ex0 + eg0;
+  return rx <= 23 && rg <= 23 && rx + rg <= 37 && mag < kCap;
+}
+
+// The oracle's code from the FP64 projection: SRP the sign, E2LSH
+// floor(((y + b) / w)) with one IEEE rounding per operation; INT32_MIN (and
+// ++novf) outside the int32 range.
+__device__ __forceinline__ int code_from_fp64(const TcArgs &a, double y64, int64_t col, int &novf) {
+  if (a.srp) return y64 > 0.0 ? 1 : 0;
+  const double f = floor(__ddiv_rn(__dadd_rn(y64, a.b64[col]), a.w));
+  if (f >= -2147483648.0 && f <= 2147483647.0) return int(f);
+  ++novf;
+  return INT32_MIN;
+}
+
+// Exact recheck of the flagged entries of one 16-column block, one entry at a
+// time by the whole warp; patches code[] of the owning lanes.
+template <bool SRP, int W>
+__device__ __forceinline__ void recheck_block(const TcArgs &a, int64_t row, int col0, uint32_t fmask, int lane,
+                                           int (&code)[W], int &nflag, int &nchanged, int &novf) {
+  for (int j = 0; j < W; ++j) {
+    uint32_t fm = __ballot_sync(0xffffffffu, (fmask >> j) & 1u);
+    while (fm) {
+      const int leader = __ffs(fm) - 1;
+      fm &= fm - 1;
+      const int64_t lrow = __shfl_sync(0xffffffffu, row, leader);
+      const int64_t col = col0 + j;
+      long long S;
+      int e;
+      const bool ok = exact_sum_group<32>(a, lrow, col, lane, S, e);
+      if (lane == leader) {
+        const int c64 = (SRP && ok) ? int(S > 0) : code_from_fp64(a, ok ? ldexp(double(S), e) : tc_fp64(a, lrow, col), col, novf);
+        ++nflag;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          if (k == j) {
+            nchanged += c64 != code[k];
+            code[k] = c64;
+          }
+      }
+    }
+  }
+}
+
+// Persistent kernel: CTA b walks output tiles b, b + gridDim.x, ... (projection
+// tile fastest, so the CTAs running at one time share their X tiles in L2).
+// The accumulators are double buffered in TMEM: the MMA warp fills buffer
+// i % 2 while the epilogue warps drain the other one.  Epilogue warp e reads
+// TMEM lanes 32 (e % 4) .. +31 (the rows it may access) and the 32-column
+// slice e / 4; M (the bins per table) is a compile-time power of two.
+template <bool SRP, int M>
+__global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                               const __grid_constant__ CUtensorMap mapB,
+                                                               const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = smem;
-  unsigned char *sB = smem + STAGES * TILE_A;
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum_full;
+  unsigned char *sA = smem;                        // the row tile: KMAX K-slices, resident per row tile
+  unsigned char *sB = smem + KMAX * TILE_A;        // G^T K-slices: SB-stage ring
+  float4 *consts = reinterpret_cast<float4 *>(smem + KMAX * TILE_A + SB * TILE_B);  // [epi warp][CONST_Q][8]
+  __shared__ __align__(8) uint64_t afull[KMAX], aempty[KMAX], bfull[SB], bempty[SB], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ float gn_s[BN][NCH];
+  __shared__ uint2 kpart[BM][2];  // M = 64: the upper slice's partial keys
+  __shared__ volatile int aborted;  // set on a timed-out wait: later waits are skipped
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t m0 = int64_t(blockIdx.x) * BM;
-  const int n0 = blockIdx.y * BN;
+  const int ntn = int(a.ML / BN);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    aborted = 0;
+    for (int k = 0; k < KMAX; ++k) {
+      mbar_init(&afull[k], 1);
+      mbar_init(&aempty[k], 1);
     }
-    mbar_init(&accum_full, 1);
+    for (int k = 0; k < SB; ++k) {
+      mbar_init(&bfull[k], 1);
+      mbar_init(&bempty[k], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < BN * NCH; i += blockDim.x) (&gn_s[0][0])[i] = a.gnc[int64_t(n0) * NCH + i];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -145,176 +325,468 @@ __global__ void __launch_bounds__(192, 1) tc_dense_kernel(const __grid_constant_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    for (int kt = 0; kt < a.ktiles; ++kt) {
-      const int s = kt % STAGES;
-      if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) {
-        atomicOr(a.status, STATUS_TIMEOUT);
-        break;
+  // Every role walks the same sequence: row tiles mt = blockIdx.x, +gridDim.x, ...
+  // and, for each, the projection tiles nt = (rot + j) % ntn, j = 0 .. ntn - 1;
+  // the rotation spreads the CTAs running at one time over all of G^T in L2.
+  const int rot = int(blockIdx.x % ntn);
+  if (warp == 0) {
+    // producer: the whole warp walks the loop, one elected lane issues
+    uint32_t it = 0, mi = 0, s = 0, sph = 0;  // B stage, and the parity of its current fill
+    bool ok = true;
+    for (int64_t mt = blockIdx.x; mt < a.mtiles && ok; mt += gridDim.x, ++mi) {
+      const int m0 = int(mt) * BM;
+      for (int j = 0; j < ntn && ok; ++j) {
+        const int n0 = ((rot + j) % ntn) * BN;
+        for (int kt = 0; kt < a.ktiles; ++kt, ++it) {
+          if (j == 0) {
+            // slot kt is free once the last MMA of the previous row tile on it completed
+            if (__any_sync(0xffffffffu, aborted != 0) || (mi >= 1 && !mbar_wait_warp(&aempty[kt], (mi - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            tma_2d_elect(sA + kt * TILE_A, &mapA, &afull[kt], TILE_A, kt * BK, m0);
+          }
+          if (__any_sync(0xffffffffu, aborted != 0) || (it >= SB && !mbar_wait_warp(&bempty[s], sph ^ 1))) {
+            ok = false;
+            break;
+          }
+          tma_2d_elect(sB + s * TILE_B, &mapB, &bfull[s], TILE_B, kt * BK, n0);
+          if (++s == SB) {
+            s = 0;
+            sph ^= 1;
+          }
+        }
       }
-      mbar_expect_tx(&full[s], TILE_A + TILE_B);
-      tma_2d(sA + s * TILE_A, &mapA, &full[s], kt * BK, int(m0));
-      tma_2d(sB + s * TILE_B, &mapB, &full[s], kt * BK, n0);
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kt = 0; kt < a.ktiles; ++kt) {
-      const int s = kt % STAGES;
-      if (!mbar_wait(&full[s], (kt / STAGES) & 1)) {
-        atomicOr(a.status, STATUS_TIMEOUT);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int chunk = kt / a.ktpc;
-      const bool first = (kt % a.ktpc) == 0;
-      const uint32_t dt = tmem + chunk * BN;
-      const uint32_t a0 = su32(sA + s * TILE_A), b0 = su32(sB + s * TILE_B);
-#pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        const uint32_t acc = (first && k == 0) ? 0u : 1u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(dt), "l"(sdesc(a0 + k * 32)), "l"(sdesc(b0 + k * 32)), "r"(idesc), "r"(acc));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&empty[s]))
-                   : "memory");
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&accum_full))
-                 : "memory");
-  } else if (warp >= 2) {
-    const int q = warp % 4;
-    if (!mbar_wait(&accum_full, 0)) {
+    if (!ok && lane == 0) {
       atomicOr(a.status, STATUS_TIMEOUT);
-    } else {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t row = m0 + q * 32 + lane;
-      const bool valid = row < a.n;
-      float xn[NCH];
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) xn[c] = valid ? a.xnc[row * NCH + c] : 0.f;
-      const bool bad = valid && !(isfinite(xn[0]) && isfinite(xn[1]) && isfinite(xn[2]) && isfinite(xn[3]));
-      const int m = a.m;
-      const int64_t ML = int64_t(m) * a.L;
-      const float steps = float(a.ktpc * (BK / 16));
-      uint32_t ha = 0, hb = 0;
-      uint64_t word = 0;
-      int nflag = 0, nchanged = 0, novf = 0;
-      for (int cb = 0; cb < BN; cb += 16) {
-        float ch[NCH][16];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          if (c < a.nch) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c * BN + cb, ch[c]);
-          else
-#pragma unroll
-            for (int j = 0; j < 16; ++j) ch[c][j] = 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int cl = cb + j;
-          const int64_t col = n0 + cl;
-          const int t = int(col / m), l = int(col - int64_t(t) * m);
-          const float y = (ch[0][j] + ch[1][j]) + (ch[2][j] + ch[3][j]);
-          float E = 2.f * kU * (fabsf(ch[0][j]) + fabsf(ch[1][j]) + fabsf(ch[2][j]) + fabsf(ch[3][j]));
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) E = fmaf(2.f * kU * steps * xn[c], gn_s[cl][c], E);
-          E *= 1.02f;
-          int code;
-          if (a.srp) {
-            code = y > 0.f ? 1 : 0;
-            if (valid && !bad && !(fabsf(y) > E)) {
-              const int c64 = tc_fp64(a, row, col) > 0.0 ? 1 : 0;
-              ++nflag;
-              nchanged += c64 != code;
-              code = c64;
-            }
-          } else {
-            const float bl = __ldg(a.b32 + col);
-            const float tf = __fmul_rn(y + bl, a.invw);
-            const float fl = floorf(tf);
-            const float fr = tf - fl;
-            const float dist = fminf(fr, 1.f - fr);
-            const float M = fmaf(E, a.invw * 1.0001f, fmaf(10.2f * kU, fabsf(tf), 15.3f * kU));
-            code = int(fl);
-            if (valid && !bad && !(dist > M && fabsf(tf) < 4194304.f)) {
-              const double t3 = __ddiv_rn(__dadd_rn(tc_fp64(a, row, col), a.b64[col]), a.w);
-              const double f = floor(t3);
-              int c64;
-              if (f >= -2147483648.0 && f <= 2147483647.0) {
-                c64 = int(f);
-              } else {
-                c64 = INT32_MIN;
-                ++novf;
-              }
-              ++nflag;
-              nchanged += c64 != code;
-              code = c64;
-            }
-            if (bad) code = INT32_MIN;
-          }
-          if (valid) {
-            if (a.proj) a.proj[row * ML + col] = y;
-            if (!a.srp && a.codes) a.codes[row * ML + col] = code;
-          }
-          if (a.srp) {
-            word |= uint64_t(code) << l;
-          } else {
-            ha += uint32_t(code) * __ldg(a.ka + col);
-            hb += uint32_t(code) * __ldg(a.kb + col);
-          }
-          if (l == m - 1) {  // the table is complete in this tile (128 % m == 0)
-            if (valid) {
-              uint64_t key = a.srp ? word : ((uint64_t(ha) << 32) | hb);
-              if (a.srp && a.bits) a.bits[row * a.L + t] = word;
-              if (bad) key = ~0ull;
-              if (a.keys) a.keys[int64_t(t) * a.key_ld + row] = key;
-            }
-            ha = hb = 0;
-            word = 0;
-          }
-        }
-      }
-      if (bad && blockIdx.y == 0) {
-        if (a.counters) atomicAdd(a.counters + CNT_NONFINITE, 1ull);
-        atomicOr(a.status, STATUS_NONFINITE);
-      }
-      if (a.counters) {
-        if (nflag) atomicAdd(a.counters + CNT_FLAGGED, (unsigned long long)nflag);
-        if (nchanged) atomicAdd(a.counters + CNT_CHANGED, (unsigned long long)nchanged);
-        if (novf) atomicAdd(a.counters + CNT_OVERFLOW, (unsigned long long)novf);
-      }
-      if (novf) atomicOr(a.status, STATUS_OVERFLOW);
+      aborted = 1;
     }
+    // let the last loads land before the CTA can exit
+    for (uint32_t k = 0; ok && k < SB && k < it; ++k) {
+      const uint32_t jj = it - 1 - k;
+      if (!mbar_wait_warp(&bfull[jj % SB], (jj / SB) & 1)) break;
+    }
+  } else if (warp == 1) {
+    // MMA issue: the whole warp walks the loop, one elected lane issues.
+    // Descriptors are precomputed and advanced by adding to their address
+    // field (shared addresses < 2^18 never carry out of it).
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    const uint64_t adesc0 = sdesc(su32(sA)), bdesc0 = sdesc(su32(sB));
+    uint32_t i = 0, mi = 0, s = 0, sph = 0;
+    bool ok = true;
+    for (int64_t mt = blockIdx.x; mt < a.mtiles && ok; mt += gridDim.x, ++mi) {
+      for (int j = 0; j < ntn && ok; ++j, ++i) {
+        const uint32_t buf = i & 1;
+        if (__any_sync(0xffffffffu, aborted != 0) || (i >= 2 && !mbar_wait_warp(&tempty[buf], ((i >> 1) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t dt = tmem + buf * (NCH * BN);
+        int kc = 0;  // K tile within the current chunk
+        for (int kt = 0; kt < a.ktiles; ++kt) {
+          if ((j == 0 && !mbar_wait_warp(&afull[kt], mi & 1)) || !mbar_wait_warp(&bfull[s], sph)) {
+            ok = false;
+            break;
+          }
+          const uint64_t ad = adesc0 + uint64_t(kt * (TILE_A >> 4)), bd = bdesc0 + uint64_t(s * (TILE_B >> 4));
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_elect(dt, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc, (kc == 0 && k == 0) ? 0u : 1u);
+          commit_elect(&bempty[s]);
+          if (j == ntn - 1) commit_elect(&aempty[kt]);
+          if (++s == SB) {
+            s = 0;
+            sph ^= 1;
+          }
+          if (++kc == a.ktpc) {
+            kc = 0;
+            dt += BN;  // the next chunk's accumulator
+          }
+        }
+        if (!ok) break;
+        commit_elect(&tfull[buf]);
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicOr(a.status, STATUS_TIMEOUT);
+      aborted = 1;
+    }
+    // wait for the last commit so that no MMA is in flight at dealloc
+    if (ok && i > 0) mbar_wait_warp(&tfull[(i - 1) & 1], ((i - 1) >> 1) & 1);
+  } else {
+    const int e = warp - 2;
+    const int q = warp % 4;
+    const int slice = e / 4;
+    // Error bound of an entry: E = xs0 g0 + xs1 g1 with xs_c = kE (steps + 1.01) ||x_c||
+    // and g_c = ||g_c|| -- the chunk sums' own rounding (kE steps ||x_c|| ||g_c||)
+    // plus that of adding them (kE (|c0| + |c1|) <= kE 1.01 sum_c ||x_c|| ||g_c||).
+    // E2LSH folds 1.0001 / w into g_c: the bound on t is then xs0 g0 + xs1 g1
+    // + 10.2 u |t| + 15.3 u.
+    const float steps = float(a.ktpc * (BK / 16));
+    const float kE = 2.f * kU * 1.02f;
+    const float invw = a.invw, gscale = SRP ? 1.f : a.invw * 1.0001f;
+    // per-column constants of this warp's slice: [g0 x8][g1 x8][b x8][ka x8][kb x8] as float4
+    float4 *cw = consts + e * (CONST_Q * 8);
+    int nflag = 0, nchanged = 0, novf = 0, nbad = 0;
+    const int64_t Tend = a.mtiles * ntn;
+    auto next_tile = [&](int64_t T) { return T + (((T + 1) % ntn == 0) ? int64_t(gridDim.x - 1) * ntn + 1 : 1); };
+    // the next tile's constants are loaded while this one is processed
+    float pg0 = 0.f, pg1 = 0.f, pb = 0.f, pka = 0.f, pkb = 0.f, px0 = 0.f, px1 = 0.f;
+    auto prefetch = [&](int64_t T) {
+      if (T >= Tend) return;
+      const int col = int((rot + T % ntn) % ntn) * BN + slice * 32 + lane;
+      const int64_t prow = (T / ntn) * BM + q * 32 + lane;
+      const float4 gq = __ldg(reinterpret_cast<const float4 *>(a.gnc + int64_t(col) * GNC_LD));
+      pg0 = gq.x;
+      pg1 = gq.y;
+      if (!SRP) {
+        pb = __ldg(a.b32 + col);
+        pka = __uint_as_float(__ldg(a.ka + col));
+        pkb = __uint_as_float(__ldg(a.kb + col));
+      }
+      px0 = px1 = 0.f;
+      if (prow < a.n) {
+        const float2 xv = __ldg(reinterpret_cast<const float2 *>(a.xnc + prow * XNC_LD));
+        px0 = xv.x;
+        px1 = xv.y;
+      }
+    };
+    prefetch(int64_t(blockIdx.x) * ntn);
+    uint32_t i = 0;
+    for (int64_t T = int64_t(blockIdx.x) * ntn; T < Tend; T = next_tile(T), ++i) {
+      const uint32_t buf = i & 1;
+      const int64_t row = int64_t(T / ntn) * BM + q * 32 + lane;
+      const int n0 = int((rot + T % ntn) % ntn) * BN + slice * 32;
+      {
+        float *cf = reinterpret_cast<float *>(cw);
+        __syncwarp();
+        cf[0 * 32 + lane] = pg0 * gscale;
+        cf[1 * 32 + lane] = pg1 * gscale;
+        if (!SRP) {
+          cf[2 * 32 + lane] = pb;
+          cf[3 * 32 + lane] = pka;
+          cf[4 * 32 + lane] = pkb;
+        }
+        __syncwarp();
+      }
+      const bool valid = row < a.n;
+      const bool bad = valid && !(isfinite(px0) && isfinite(px1));
+      const float xs[NCH] = {kE * (steps + 1.01f) * px0, kE * (steps + 1.01f) * px1};
+      if (bad && n0 == 0) ++nbad;
+      prefetch(next_tile(T));
+      // on a timeout the warp goes on without waiting (the status reports the
+      // failure), so that every epilogue warp reaches the same named barriers
+      if (!aborted && !mbar_wait(&tfull[buf], (i >> 1) & 1, 2000)) {
+        atomicOr(a.status, STATUS_TIMEOUT);
+        aborted = 1;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * (NCH * BN) + slice * 32;
+      uint32_t ha = 0, hb = 0, word = 0;
+#pragma unroll 1
+      for (int blk = 0; blk < 32 / BW; ++blk) {
+        float ch[NCH][BW];
+        {
+          uint32_t r0[BW], r1[BW];
+          tmem_ld8_nowait(taddr + blk * BW, r0);
+          if (a.nch > 1) tmem_ld8_nowait(taddr + BN + blk * BW, r1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < BW; ++j) {
+            ch[0][j] = __uint_as_float(r0[j]);
+            ch[1][j] = a.nch > 1 ? __uint_as_float(r1[j]) : 0.f;
+          }
+        }
+        if (blk == 32 / BW - 1) {
+          // every accumulator of this buffer is in registers: hand it back to the MMA warp
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        const int col0 = n0 + blk * BW;
+        int code[BW];
+        uint32_t fmask = 0;
+        // 1. fast codes and the entries within the error bound
+#pragma unroll
+        for (int g4 = 0; g4 < BW / 4; ++g4) {
+          const int q4 = blk * (BW / 4) + g4;  // float4 index within the slice
+          const float4 g0 = cw[0 * 8 + q4], g1 = cw[1 * 8 + q4];
+          float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (!SRP) bb = cw[2 * 8 + q4];
+          const float gg0[4] = {g0.x, g0.y, g0.z, g0.w}, gg1[4] = {g1.x, g1.y, g1.z, g1.w};
+          const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = g4 * 4 + u;
+            const float y = ch[0][j] + ch[1][j];
+            bool flag;
+            if (SRP) {
+              const float E = fmaf(xs[0], gg0[u], xs[1] * gg1[u]);
+              code[j] = y > 0.f ? 1 : 0;
+              flag = !(fabsf(y) > E);
+            } else {
+              const float tf = __fmul_rn(y + bv[u], invw);
+              const float dist = fabsf(tf - rintf(tf));  // exact
+              const float Mb = fmaf(xs[0], gg0[u], fmaf(xs[1], gg1[u], fmaf(10.2f * kU, fabsf(tf), 15.3f * kU)));
+              code[j] = __float2int_rd(tf);
+              flag = !(dist > Mb && fabsf(tf) < 4194304.f);
+            }
+            if (flag) fmask |= 1u << j;
+          }
+        }
+        if (a.proj && valid)
+#pragma unroll
+          for (int j = 0; j < BW; j += 4)
+            *reinterpret_cast<float4 *>(a.proj + row * a.ML + col0 + j) =
+                make_float4(ch[0][j] + ch[1][j], ch[0][j + 1] + ch[1][j + 1], ch[0][j + 2] + ch[1][j + 2],
+                            ch[0][j + 3] + ch[1][j + 3]);
+        if (!valid || bad) fmask = 0;
+        // 2. the rare slow path: queue the flagged entries for the recheck
+        //    kernel; entries beyond the queue's capacity are rechecked here
+        if (__any_sync(0xffffffffu, fmask != 0)) {
+          const uint32_t cnt = __popc(fmask);
+          uint32_t incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          uint32_t base = 0;
+          if (lane == 31) base = atomicAdd(a.qcount, incl);
+          uint32_t pos = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+          uint32_t over = 0;
+#pragma unroll
+          for (int j = 0; j < BW; ++j)
+            if ((fmask >> j) & 1u) {
+              if (pos < a.qcap) a.queue[pos] = make_int4(int(row), col0 + j, code[j], 0);
+              else over |= 1u << j;
+              ++pos;
+            }
+          if (__any_sync(0xffffffffu, over != 0))
+            recheck_block<SRP, BW>(a, row, col0, over, lane, code, nflag, nchanged, novf);
+        }
+        // 3. codes out, key fold
+        if (!SRP && a.codes && valid) {
+          int4 *dst = reinterpret_cast<int4 *>(a.codes + row * a.ML + col0);
+#pragma unroll
+          for (int j = 0; j < BW; j += 4)
+            dst[j / 4] = bad ? make_int4(INT32_MIN, INT32_MIN, INT32_MIN, INT32_MIN)
+                             : make_int4(code[j], code[j + 1], code[j + 2], code[j + 3]);
+        }
+        uint32_t wb = 0;  // SRP bits of this block
+#pragma unroll
+        for (int g4 = 0; g4 < BW / 4; ++g4) {
+          const int q4 = blk * (BW / 4) + g4;
+          uint4 kav = make_uint4(0, 0, 0, 0), kbv = make_uint4(0, 0, 0, 0);
+          if (!SRP) {
+            const float4 fa = cw[3 * 8 + q4], fb = cw[4 * 8 + q4];
+            kav = make_uint4(__float_as_uint(fa.x), __float_as_uint(fa.y), __float_as_uint(fa.z), __float_as_uint(fa.w));
+            kbv = make_uint4(__float_as_uint(fb.x), __float_as_uint(fb.y), __float_as_uint(fb.z), __float_as_uint(fb.w));
+          }
+          const uint32_t kav4[4] = {kav.x, kav.y, kav.z, kav.w}, kbv4[4] = {kbv.x, kbv.y, kbv.z, kbv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = g4 * 4 + u;  // column within the block (static)
+            if (SRP) {
+              wb |= uint32_t(code[j]) << j;
+            } else {
+              ha += uint32_t(code[j]) * kav4[u];
+              hb += uint32_t(code[j]) * kbv4[u];
+            }
+            // does a table end at this column?  static for M <= BW, one test per block otherwise
+            const bool ends = M <= BW ? (j % M == M - 1) : (j == BW - 1 && ((blk + 1) * BW) % M == 0);
+            if (ends && M <= 32) {
+              const int jj = blk * BW + j;  // column within the slice
+              uint64_t bitsv = 0;
+              if (SRP) {
+                const uint32_t wfull = word | (wb << (blk * BW));
+                bitsv = uint64_t(wfull >> (jj + 1 - M)) & (M == 32 ? 0xFFFFFFFFull : ((1ull << (M & 31)) - 1));
+              }
+              if (valid) {
+                const int t = (n0 + jj) / M;
+                if (SRP && a.bits) a.bits[row * a.L + t] = bitsv;
+                if (a.keys) a.keys[int64_t(t) * a.key_ld + row] = bad ? ~0ull : (SRP ? bitsv : ((uint64_t(ha) << 32) | hb));
+              }
+              ha = hb = 0;
+            }
+          }
+        }
+        if (SRP) word |= wb << (blk * BW);
+      }
+      if (M == 64) {
+        // a table spans slices (0, 1) or (2, 3): the odd slice hands its partial key to the even one
+        const int r = q * 32 + lane;
+        if (slice & 1) kpart[r][slice >> 1] = make_uint2(SRP ? word : ha, hb);
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+        if (!(slice & 1) && valid) {
+          const uint2 o = kpart[r][slice >> 1];
+          const int t = n0 / 64;
+          uint64_t key;
+          if (SRP) {
+            key = uint64_t(word) | (uint64_t(o.x) << 32);
+            if (a.bits) a.bits[row * a.L + t] = key;
+          } else {
+            key = (uint64_t(ha + o.x) << 32) | (hb + o.y);
+          }
+          if (bad) key = ~0ull;
+          if (a.keys) a.keys[int64_t(t) * a.key_ld + row] = key;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+      }
+    }
+    if (nbad) {
+      if (a.counters) atomicAdd(a.counters + CNT_NONFINITE, (unsigned long long)nbad);
+      atomicOr(a.status, STATUS_NONFINITE);
+    }
+    if (a.counters) {
+      if (nflag) atomicAdd(a.counters + CNT_FLAGGED, (unsigned long long)nflag);
+      if (nchanged) atomicAdd(a.counters + CNT_CHANGED, (unsigned long long)nchanged);
+      if (novf) atomicAdd(a.counters + CNT_OVERFLOW, (unsigned long long)novf);
+    }
+    if (novf) atomicOr(a.status, STATUS_OVERFLOW);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// Row chunk norms ||x_chunk||, widened to an upper bound; NaN when the row is not finite.
+// The queued entries, 32 to a warp: the whole warp computes the exact sum of
+// each entry in turn (lane k keeps entry k's), then every lane converts and
+// discretises its own entry -- the FP64 steps run once for 32 entries -- and
+// patches, where the fast code was wrong, the code, the SRP bits and the key.
+// E2LSH keys are sums mod 2^32 in both halves, so a changed code c -> c' adds
+// (c' - c) ka and (c' - c) kb.  Entries whose exactness condition fails take
+// the sequential FP64 loop in their own lane.
+__global__ void __launch_bounds__(256) tc_recheck_kernel(const TcArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t cnt = min(*a.qcount, a.qcap);
+  int nflag = 0, nchanged = 0, novf = 0;
+  for (int64_t base = w0 * 32; base < cnt; base += nw * 32) {
+    const bool mine = base + lane < cnt;
+    const int4 r = mine ? a.queue[base + lane] : make_int4(0, 0, 0, 0);
+    const int nb = int(min(int64_t(32), cnt - base));
+    long long Sm = 0;
+    int em = 0;
+    bool okm = false;
+    // four entries at a time, eight lanes each: entry 4k + lane / 8
+    for (int k = 0; k < (nb + 3) / 4; ++k) {
+      const int src = min(4 * k + (lane >> 3), nb - 1);
+      const int64_t row = __shfl_sync(0xffffffffu, r.x, src), col = __shfl_sync(0xffffffffu, r.y, src);
+      long long S;
+      int e;
+      const bool ok = exact_sum_group<8>(a, row, col, lane & 7, S, e);
+      // lane 4k + g takes the result of group g (held by its lane 8g)
+      const int from = (min(max(lane - 4 * k, 0), 3)) * 8;
+      const long long Sg = __shfl_sync(0xffffffffu, S, from);
+      const int eg = __shfl_sync(0xffffffffu, e, from);
+      const bool okg = __shfl_sync(0xffffffffu, ok ? 1 : 0, from) != 0;
+      if (lane >= 4 * k && lane < 4 * k + 4) {
+        Sm = Sg;
+        em = eg;
+        okm = okg;
+      }
+    }
+    if (mine) {
+      const int64_t row = r.x, col = r.y;
+      const int c64 = (a.srp && okm) ? int(Sm > 0)
+                                     : code_from_fp64(a, okm ? ldexp(double(Sm), em) : tc_fp64(a, row, col), col, novf);
+      ++nflag;
+      if (c64 != r.z) {
+        ++nchanged;
+        const int t = int(col / a.m), l = int(col - int64_t(t) * a.m);
+        uint64_t *key = a.keys ? a.keys + int64_t(t) * a.key_ld + row : nullptr;
+        if (a.srp) {
+          if (key) atomicXor(reinterpret_cast<unsigned long long *>(key), 1ull << l);
+          if (a.bits) atomicXor(reinterpret_cast<unsigned long long *>(a.bits + row * a.L + t), 1ull << l);
+        } else {
+          if (a.codes) a.codes[row * a.ML + col] = c64;
+          const uint32_t dc = uint32_t(c64) - uint32_t(r.z);
+          if (key) {
+            atomicAdd(reinterpret_cast<unsigned int *>(key) + 1, dc * a.ka[col]);
+            atomicAdd(reinterpret_cast<unsigned int *>(key), dc * a.kb[col]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nflag += __shfl_xor_sync(0xffffffffu, nflag, o);
+    nchanged += __shfl_xor_sync(0xffffffffu, nchanged, o);
+    novf += __shfl_xor_sync(0xffffffffu, novf, o);
+  }
+  if (lane == 0) {
+    if (a.counters) {
+      if (nflag) atomicAdd(a.counters + CNT_FLAGGED, (unsigned long long)nflag);
+      if (nchanged) atomicAdd(a.counters + CNT_CHANGED, (unsigned long long)nchanged);
+      if (novf) atomicAdd(a.counters + CNT_OVERFLOW, (unsigned long long)novf);
+    }
+    if (novf) atomicOr(a.status, STATUS_OVERFLOW);
+  }
+}
+
+// Row records: chunk norms ||x_chunk|| widened to an upper bound (NaN when
+// the row is not finite), then the least exponent and the exponent range of
+// the nonzero coordinates (x = M 2^E, M < 256).  Warp per row, 16-byte loads
+// (d and the row stride are multiples of eight on this path).
 __global__ void __launch_bounds__(256) row_chunk_norms(const unsigned short *X, int64_t n, int d, int64_t ld,
                                                        int chunk_len, float *out) {
   const int64_t row = int64_t(blockIdx.x) * 8 + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= n) return;
-  float s[NCH] = {0.f, 0.f, 0.f, 0.f};
+  float s[NCH];
+#pragma unroll
+  for (int cc = 0; cc < NCH; ++cc) s[cc] = 0.f;
   bool fin = true;
-  for (int j = lane; j < d; j += 32) {
-    const float v = __uint_as_float(uint32_t(X[row * ld + j]) << 16);
-    fin = fin && isfinite(v);
-    const int c = min(j / chunk_len, NCH - 1);
+  int emin = 1 << 20, emax = -(1 << 20);
+  const uint4 *xr = reinterpret_cast<const uint4 *>(X + row * ld);
+  for (int c = lane; c < (d >> 3); c += 32) {
+    const uint4 v4 = xr[c];
+    const uint32_t w[4] = {v4.x, v4.y, v4.z, v4.w};
+    const int ch = min((c * 8) / chunk_len, NCH - 1);
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t h = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+      const float v = __uint_as_float(h << 16);
+      fin = fin && isfinite(v);
+      acc = fmaf(v, v, acc);
+      const int e = (h >> 7) & 0xFF;
+      if (h & 0x7FFF) {
+        const int E = max(e, 1) - 134;
+        emin = min(emin, E);
+        emax = max(emax, E);
+      }
+    }
 #pragma unroll
     for (int cc = 0; cc < NCH; ++cc)
-      if (cc == c) s[cc] = fmaf(v, v, s[cc]);
+      if (cc == ch) s[cc] += acc;
   }
 #pragma unroll
-  for (int cc = 0; cc < NCH; ++cc)
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[cc] += __shfl_xor_sync(0xffffffffu, s[cc], o);
+    for (int cc = 0; cc < NCH; ++cc) s[cc] += __shfl_xor_sync(0xffffffffu, s[cc], o);
+    emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
   const bool allfin = __all_sync(0xffffffffu, fin);
+  if (emax < emin) emin = emax = 0;  // an all-zero row
   if (lane < NCH) {
+    float v = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < NCH; ++cc)
+      if (cc == lane) v = s[cc];
+    // FP32 sum of squares of at most d terms: relative error below (d + 8) u
     const float widen = 1.f + float(d + 8) * kU;
-    out[row * NCH + lane] = allfin ? sqrtf(s[lane] * widen) * (1.f + 2.f * kU) : __int_as_float(0x7fc00000);
+    out[row * XNC_LD + lane] = allfin ? sqrtf(v * widen) * (1.f + 2.f * kU) : __int_as_float(0x7fc00000);
+  } else if (lane == 2) {
+    out[row * XNC_LD + 2] = __int_as_float(emin);
+  } else if (lane == 3) {
+    out[row * XNC_LD + 3] = __int_as_float(emax - emin);
   }
 }
 
@@ -355,29 +827,49 @@ int tc_chunk_ktiles(int d) {
   return (ktiles + NCH - 1) / NCH;
 }
 
+// Scratch of one call: the row records [n][4] floats, the queue counter and
+// the recheck queue (16 bytes an entry, about 4x the flag rate seen on
+// Gaussian data; entries beyond it are rechecked inside the main kernel).
+static int64_t tc_queue_cap(int64_t n, int64_t ML) {
+  return std::min<int64_t>(n * ML / 1024 + 65536, int64_t(1) << 28);
+}
+static int64_t tc_align16(int64_t b) { return (b + 15) & ~int64_t(15); }
+
+size_t tc_dense_scratch_bytes(int64_t n, int64_t ML) {
+  return size_t(tc_align16(n * XNC_LD * 4) + 16 + tc_queue_cap(n, ML) * 16);
+}
+
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X) {
   const int64_t ML = int64_t(fd.m) * fd.L;
   if (!kind_is_dense(fd.kind) || fd.compute != LSH_BF16 || !X || X->rowptr || X->dtype != LSH_BF16) return false;
   if (fd.d % 8 != 0 || X->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(X->values) & 15) != 0) return false;
-  if (ML % BN != 0 || BN % fd.m != 0 || (kind_is_srp(fd.kind) && fd.m > 64)) return false;
+  if (ML % BN != 0 || 64 % fd.m != 0) return false;  // a 32-column slice or a pair of them holds whole tables
+  if (fd.d > KMAX * BK) return false;                 // the row tile stays resident in shared memory
   if (X->n > (int64_t(1) << 31) - BM || (X->n + BM - 1) / BM > 2147483647) return false;
   return encode_fn() != nullptr;
 }
 
 cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
-                            float *xnc_scratch, cudaStream_t stream) {
+                            const int32_t *Gint, void *scratch, cudaStream_t stream) {
   if (p.n <= 0) return cudaSuccess;
   const int ktiles = (p.d + BK - 1) / BK;
   const int ktpc = tc_chunk_ktiles(p.d);
   const int64_t ML = int64_t(p.m) * p.L;
+  float *xnc_scratch = static_cast<float *>(scratch);
+  uint32_t *qcount = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + tc_align16(p.n * XNC_LD * 4));
+  int4 *queue = reinterpret_cast<int4 *>(qcount + 4);
+  cudaError_t e = cudaMemsetAsync(qcount, 0, 16, stream);
+  if (e != cudaSuccess) return e;
   row_chunk_norms<<<(unsigned)((p.n + 7) / 8), 256, 0, stream>>>(static_cast<const unsigned short *>(p.X), p.n, p.d,
                                                                    p.ld, ktpc * BK, xnc_scratch);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!make_map(&mA, p.X, p.n, p.d, p.ld) || !make_map(&mB, Gt16, ML, p.d, p.d)) return cudaErrorInvalidValue;
   TcArgs a{};
   a.n = p.n;
+  a.mtiles = (p.n + BM - 1) / BM;
+  a.ML = ML;
   a.d = p.d;
   a.m = p.m;
   a.L = p.L;
@@ -388,6 +880,7 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, c
   a.X = static_cast<const unsigned short *>(p.X);
   a.ld = p.ld;
   a.Gt = Gt;
+  a.Gint = Gint;
   a.gnc = gnc;
   a.xnc = xnc_scratch;
   a.b32 = p.b32;
@@ -403,12 +896,30 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, c
   a.proj = p.proj;
   a.counters = p.counters;
   a.status = p.status;
-  const int smem = STAGES * (TILE_A + TILE_B) + 1024;
-  e = cudaFuncSetAttribute(tc_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  a.queue = queue;
+  a.qcount = qcount;
+  a.qcap = uint32_t(tc_queue_cap(p.n, ML));
+  const int smem = KMAX * TILE_A + SB * TILE_B + 1024 + kEpiWarps * CONST_Q * 8 * 16;
+  void (*kern)(const CUtensorMap, const CUtensorMap, const TcArgs) = nullptr;
+  switch (p.m * 2 + a.srp) {
+#define LSH_TC_CASE(M)                              \
+  case 2 * M: kern = tc_dense_kernel<false, M>; break; \
+  case 2 * M + 1: kern = tc_dense_kernel<true, M>; break;
+    LSH_TC_CASE(1) LSH_TC_CASE(2) LSH_TC_CASE(4) LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
+#undef LSH_TC_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((p.n + BM - 1) / BM), (unsigned)(ML / BN));
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  tc_dense_kernel<<<grid, 192, smem, stream>>>(mA, mB, a);
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(a.mtiles, sms);
+  kern<<<grid, kThreads, smem, stream>>>(mA, mB, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  tc_recheck_kernel<<<unsigned(sms) * 8, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -56,11 +56,13 @@ def log_uniform_sizes(n: int, hi: int, rng: np.random.Generator):
     return np.clip(np.floor(np.exp(rng.uniform(0, math.log(hi + 1), size=n))).astype(np.int64), 1, hi)
 
 
-def run_load(server, Qpool: torch.Tensor, sizes, rate_qps: float | None, rng: np.random.Generator):
+def run_load(server, Qpool: torch.Tensor, sizes, rate_qps: float | None, rng: np.random.Generator,
+             max_seconds: float | None = None):
     """Submit batches of the given sizes (rows drawn from Qpool) with Poisson
     arrivals at `rate_qps` queries per second (None: back to back, keeping the
     loop saturated); a second thread waits for completions.  Returns
-    (queries/s over the run, per-request latencies in ms)."""
+    (queries/s over the run, per-request latencies in ms).  With max_seconds,
+    no request is submitted after that much time has passed."""
     Qh = Qpool.cpu().contiguous()
     nq = Qh.shape[0]
     starts = rng.integers(0, max(1, nq - int(max(sizes))), size=len(sizes))
@@ -75,13 +77,12 @@ def run_load(server, Qpool: torch.Tensor, sizes, rate_qps: float | None, rng: np
             with lock:
                 have = i < len(tickets)
                 t = tickets[i] if have else None
+                finished = done_evt.is_set() and i >= len(tickets)
             if have:
                 _, _, ms = server.wait(t)
                 lat.append(ms)
                 i += 1
-                if i == len(sizes):
-                    break
-            elif done_evt.is_set() and i >= len(tickets):
+            elif finished:
                 break
             else:
                 time.sleep(5e-5)
@@ -92,6 +93,8 @@ def run_load(server, Qpool: torch.Tensor, sizes, rate_qps: float | None, rng: np
     next_t = t0
     total = 0
     for b, s0 in zip(sizes, starts):
+        if max_seconds is not None and time.perf_counter() - t0 > max_seconds:
+            break
         if rate_qps:
             next_t += rng.exponential(b / rate_qps)
             dt = next_t - time.perf_counter()
@@ -104,4 +107,4 @@ def run_load(server, Qpool: torch.Tensor, sizes, rate_qps: float | None, rng: np
     done_evt.set()
     th.join()
     el = time.perf_counter() - t0
-    return total / el, np.array(lat)
+    return total / el, np.array(lat) if lat else np.zeros(1)

@@ -74,3 +74,43 @@ def test_dense_bf16_tensor_core_equals_simt_path():
     a = fam.hash(X[:, :512].contiguous(), codes=True, keys=True)
     b = fam.hash(X[:, :512], codes=True, keys=True)
     assert torch.equal(a["codes"], b["codes"]) and torch.equal(a["keys"], b["keys"])
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+def test_dense_bf16_tensor_core_many_tiles_per_cta(kind):
+    """More output tiles than SMs: each persistent CTA walks several tiles
+    through both TMEM accumulator buffers."""
+    X = workloads.iid(20000, 128, seed=12, device="cpu", dtype=torch.bfloat16).cuda()
+    compare_hash(dict(kind=kind, d=128, m=16, L=16, w=4.0, seed=8, compute=1), X)
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+def test_dense_bf16_tensor_core_wide_exponents(kind):
+    """Rows whose coordinates span ~2^40 in magnitude: flagged entries there
+    fail the fixed-point exactness condition (product exponents more than 37
+    apart) and take the sequential FP64 loop."""
+    X = workloads.iid(600, 256, seed=13, device="cpu", dtype=torch.float32)
+    g = torch.Generator().manual_seed(5)
+    X[::3] *= torch.exp2(torch.randint(-12, 13, X[::3].shape, generator=g).float())
+    X = X.to(torch.bfloat16).cuda()
+    compare_hash(dict(kind=kind, d=256, m=32, L=8, w=4.0, seed=9, compute=1), X)
+
+
+def test_dense_bf16_tensor_core_nonfinite_row():
+    X = workloads.iid(300, 128, seed=14, device="cpu", dtype=torch.bfloat16).cuda()
+    X[7, 100] = float("inf")
+    fam = lsh.Family("e2lsh", 128, 16, 16, w=4.0, seed=2, compute=1)
+    with pytest.raises(lsh.LshError):
+        fam.hash(X, keys=True, stats=True)
+    k = fam.hash(X, keys=True)["keys"].cpu().numpy().view(np.uint64)
+    assert (k[:, 7] == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    good = torch.as_tensor(np.setdiff1d(np.arange(300), [7])).cuda()
+    compare_hash(dict(kind="e2lsh", d=128, m=16, L=16, w=4.0, seed=2, compute=1), X[good])
+
+
+def test_dense_bf16_tensor_core_recheck_queue_overflow():
+    """Bins narrower than the error bound flag every entry: more than the
+    recheck queue holds, so part of them is rechecked inside the main kernel."""
+    X = workloads.iid(300, 512, seed=15, device="cpu", dtype=torch.bfloat16).cuda()
+    stats, _ = compare_hash(dict(kind="e2lsh", d=512, m=32, L=8, w=1e-4, seed=4, compute=1), X)
+    assert stats["n_flagged"] >= 0.9 * 300 * 256
