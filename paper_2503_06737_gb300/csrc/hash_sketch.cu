@@ -36,6 +36,8 @@
 //     A max|x| of 0 (SRP, A without sqrt(m)/w), is recomputed by its lane in
 //     FP64 from the same staged tile, in ascending j, one IEEE rounding per
 //     operation: the canonical value of Definitions 12/19/25/31.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,6 +50,7 @@ namespace {
 constexpr int kWarp = 32;
 constexpr float kU32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of FP32
 constexpr int kMaxSmem = 232448;                 // 227 KB opt-in per block
+constexpr int kLoadBatch = 16;                   // row-tile loads in flight per lane
 
 struct Plan {
   int Lg, G, RG, WPT, W, smem;
@@ -97,7 +100,8 @@ __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, i
 // Stage table t (one warp): member list (sign-split, quad-padded) and the
 // per-bin records seg[l] = {start, quads(+) | quads(-) << 16},
 // cst[l] = {b_l (f32 bits), A_l, ka_l, kb_l}.
-__device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_t *ent, uint2 *seg,
+template <typename EntT>
+__device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *ent, uint2 *seg,
                             uint4 *cst, uint32_t *scratch, int lane) {
   const int d = p.d, m = p.m;
   uint32_t *cur = scratch;  // [2m]: counts, then write cursors (key = 2 bin + neg)
@@ -130,8 +134,8 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
     if (l < m) {
       const uint32_t qp = (cp + 3) & ~3u, qn = (cn + 3) & ~3u;
       seg[l] = make_uint2(start, (qp >> 2) | ((qn >> 2) << 16));
-      for (uint32_t i = cp; i < qp; ++i) ent[start + i] = zslot;
-      for (uint32_t i = cn; i < qn; ++i) ent[start + qp + i] = zslot;
+      for (uint32_t i = cp; i < qp; ++i) ent[start + i] = EntT(zslot);
+      for (uint32_t i = cn; i < qn; ++i) ent[start + qp + i] = EntT(zslot);
       cur[2 * l] = start;
       cur[2 * l + 1] = start + qp;
       const float k = float(cp + cn);
@@ -154,12 +158,28 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
       coord_bin(p, t, j, bin, neg);
       const uint32_t key = 2u * uint32_t(bin) + neg;
       const uint32_t peers = __match_any_sync(amask, key);
-      ent[cur[key] + __popc(peers & lt)] = uint32_t(j) << 2;
+      ent[cur[key] + __popc(peers & lt)] = EntT(uint32_t(j) << 2);
       __syncwarp(amask);
       if ((peers & lt) == 0) cur[key] += __popc(peers);
     }
     __syncwarp();
   }
+}
+
+// Four member offsets (bytes into the row) at quad q of a list.
+__device__ __forceinline__ void load_quad(const uint32_t *E, int q, uint32_t (&o)[4]) {
+  const uint4 v = reinterpret_cast<const uint4 *>(E)[q];
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void load_quad(const uint16_t *E, int q, uint32_t (&o)[4]) {
+  const uint2 v = reinterpret_cast<const uint2 *>(E)[q];
+  o[0] = v.x & 0xFFFFu;
+  o[1] = v.x >> 16;
+  o[2] = v.y & 0xFFFFu;
+  o[3] = v.y >> 16;
 }
 
 __device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off) {
@@ -168,7 +188,8 @@ __device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off
 
 // FP64 recheck of one bin for this lane: merge the two ascending halves back
 // into ascending j and sum s(j) x_j with one IEEE rounding per addition.
-__device__ __noinline__ double bin_fp64(const uint32_t *P, int np, const uint32_t *N, int nn,
+template <typename EntT>
+__device__ __noinline__ double bin_fp64(const EntT *P, int np, const EntT *N, int nn,
                                         const unsigned char *xr, uint32_t zslot) {
   int ip = 0, in = 0;
   double y = 0.0;
@@ -187,7 +208,78 @@ __device__ __noinline__ double bin_fp64(const uint32_t *P, int np, const uint32_
   return y;
 }
 
-template <bool SRP, int DT>
+// The same FP64 value without the sequential loop, when the bin's terms
+// allow it: an FP32 value is M 2^E with |M| < 2^24 an integer; with the
+// bin's least exponent E0 every term is an integer multiple of 2^E0, and if
+// the exponents span at most 29 and the magnitudes sum to less than 2^53
+// (in units of 2^E0), every partial sum of the ascending FP64 loop is exact,
+// so that loop returns the exact sum -- which int64 addition gets in any
+// order.  Returns false (the caller runs the loop) when a condition fails.
+__device__ __forceinline__ void fp32_parts(uint32_t v, int &E, uint32_t &M) {
+  const int e = int((v >> 23) & 0xFF);
+  E = max(e, 1) - 150;
+  M = (v & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+}
+template <typename EntT>
+__device__ __noinline__ bool bin_exact(const EntT *P, int np, const EntT *N, int nn,
+                                       const unsigned char *xr, double &y) {
+  int emin = 1 << 20, emax = -(1 << 20);
+  for (int h = 0; h < 2; ++h) {
+    const EntT *L = h ? N : P;
+    const int k = h ? nn : np;
+    for (int i = 0; i < k; ++i) {
+      const uint32_t v = __float_as_uint(lds_f32(xr, L[i]));
+      if (v & 0x7FFFFFFFu) {
+        int E;
+        uint32_t M;
+        fp32_parts(v, E, M);
+        emin = min(emin, E);
+        emax = max(emax, E);
+      }
+    }
+  }
+  if (emax < emin) {
+    y = 0.0;
+    return true;
+  }
+  if (emax - emin > 29) return false;
+  constexpr unsigned long long kCap = 1ull << 53;
+  unsigned long long sum = 0, mag = 0;  // two's complement sum; saturating magnitude
+  for (int h = 0; h < 2; ++h) {
+    const EntT *L = h ? N : P;
+    const int k = h ? nn : np;
+    for (int i = 0; i < k; ++i) {
+      const uint32_t v = __float_as_uint(lds_f32(xr, L[i]));
+      int E;
+      uint32_t M;
+      fp32_parts(v, E, M);
+      const unsigned long long t = (unsigned long long)M << max(E - emin, 0);  // zero stays zero
+      sum += ((v >> 31) ^ uint32_t(h)) ? 0ull - t : t;
+      mag = min(mag + t, kCap);
+    }
+  }
+  if (mag >= kCap) return false;
+  y = ldexp(double((long long)sum), emin);
+  return true;
+}
+
+// Append this lane's flagged bin to the recheck queue (warp-aggregated);
+// false when there is no queue or it is full (the lane then rechecks in place).
+__device__ __forceinline__ bool queue_bin(const SketchLaunch &p, bool flag, int64_t row, int t, int l, int code,
+                                          int lane) {
+  if (!p.queue) return false;
+  const uint32_t bal = __ballot_sync(0xffffffffu, flag);
+  const int leader = __ffs(bal) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(p.qcount, uint32_t(__popc(bal)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  const uint32_t pos = base + __popc(bal & ((1u << lane) - 1u));
+  if (!flag || pos >= p.qcap) return false;
+  p.queue[pos] = make_int4(int(row), t, l, code);
+  return true;
+}
+
+template <bool SRP, int DT, typename EntT>
 __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SketchLaunch &p = a.p;
@@ -203,7 +295,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
   const int cap = pl.cap;
   const int WPT = pl.WPT;
 
-  uint32_t *ent = reinterpret_cast<uint32_t *>(smem + pl.off_ent);
+  EntT *ent = reinterpret_cast<EntT *>(smem + pl.off_ent);
   uint2 *seg = reinterpret_cast<uint2 *>(smem + pl.off_seg);
   uint4 *cst = reinterpret_cast<uint4 *>(smem + pl.off_cst);
   uint2 *kacc = reinterpret_cast<uint2 *>(smem + pl.off_key);  // [R][Lg] partial keys
@@ -227,7 +319,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
 
   for (int tile = slot; tile < a.ntiles; tile += a.slots) {
     const int64_t row0 = int64_t(tile) * R;
-    // ---- load the row tile (warp per row, coalesced, 8 loads in flight) ----
+    // ---- load the row tile (warp per row, coalesced, kLoadBatch loads in flight) ----
     for (int r = warp; r < R; r += pl.W) {
       const int64_t row = row0 + r;
       float *dst = xs + r * xst;
@@ -235,15 +327,15 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       bool fin = true;
       if (row < p.n) {
         const int64_t base = row * p.ld;
-        for (int j0 = lane; j0 < d; j0 += 8 * kWarp) {
-          float v[8];
+        for (int j0 = lane; j0 < d; j0 += kLoadBatch * kWarp) {
+          float v[kLoadBatch];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < kLoadBatch; ++u) {
             const int j = j0 + u * kWarp;
             v[u] = j < d ? load_x<DT>(p.X, base + j) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < kLoadBatch; ++u) {
             const int j = j0 + u * kWarp;
             if (j < d) dst[j] = v[u];
             mx = fmaxf(mx, fabsf(v[u]));
@@ -290,7 +382,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       const bool isbad = bad[r] != 0;
       const float xm = xmax[r];
       const unsigned char *xr = reinterpret_cast<const unsigned char *>(xs + r * xst);
-      const uint32_t *E = ent + tl * cap;
+      const EntT *E = ent + tl * cap;
       const uint2 *S = seg + tl * m;
       const uint4 *C = cst + tl * m;
       uint32_t ha = 0, hb = 0;
@@ -299,24 +391,55 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       for (int l = sub; l < m; l += WPT) {
         const uint2 sg = S[l];
         const int qp = int(sg.y & 0xffffu), qn = int(sg.y >> 16);
-        const uint4 *Q = reinterpret_cast<const uint4 *>(E + sg.x);
+        const EntT *Q = E + sg.x;
+        // two quads per iteration (eight loads in flight), then the odd quad
         float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        int q = 0;
 #pragma unroll 1
-        for (int q = 0; q < qp; ++q) {
-          const uint4 e = Q[q];
-          p0 += lds_f32(xr, e.x);
-          p1 += lds_f32(xr, e.y);
-          p2 += lds_f32(xr, e.z);
-          p3 += lds_f32(xr, e.w);
+        for (; q + 2 <= qp; q += 2) {
+          uint32_t e[4], f[4];
+          load_quad(Q, q, e);
+          load_quad(Q, q + 1, f);
+          p0 += lds_f32(xr, e[0]);
+          p1 += lds_f32(xr, e[1]);
+          p2 += lds_f32(xr, e[2]);
+          p3 += lds_f32(xr, e[3]);
+          p0 += lds_f32(xr, f[0]);
+          p1 += lds_f32(xr, f[1]);
+          p2 += lds_f32(xr, f[2]);
+          p3 += lds_f32(xr, f[3]);
+        }
+        if (q < qp) {
+          uint32_t e[4];
+          load_quad(Q, q, e);
+          p0 += lds_f32(xr, e[0]);
+          p1 += lds_f32(xr, e[1]);
+          p2 += lds_f32(xr, e[2]);
+          p3 += lds_f32(xr, e[3]);
         }
         float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+        q = qp;
 #pragma unroll 1
-        for (int q = qp; q < qp + qn; ++q) {
-          const uint4 e = Q[q];
-          n0 += lds_f32(xr, e.x);
-          n1 += lds_f32(xr, e.y);
-          n2 += lds_f32(xr, e.z);
-          n3 += lds_f32(xr, e.w);
+        for (; q + 2 <= qp + qn; q += 2) {
+          uint32_t e[4], f[4];
+          load_quad(Q, q, e);
+          load_quad(Q, q + 1, f);
+          n0 += lds_f32(xr, e[0]);
+          n1 += lds_f32(xr, e[1]);
+          n2 += lds_f32(xr, e[2]);
+          n3 += lds_f32(xr, e[3]);
+          n0 += lds_f32(xr, f[0]);
+          n1 += lds_f32(xr, f[1]);
+          n2 += lds_f32(xr, f[2]);
+          n3 += lds_f32(xr, f[3]);
+        }
+        if (q < qp + qn) {
+          uint32_t e[4];
+          load_quad(Q, q, e);
+          n0 += lds_f32(xr, e[0]);
+          n1 += lds_f32(xr, e[1]);
+          n2 += lds_f32(xr, e[2]);
+          n3 += lds_f32(xr, e[3]);
         }
         const float y = ((p0 + p1) + (p2 + p3)) - ((n0 + n1) + (n2 + n3));
         const uint4 c = C[l];
@@ -326,9 +449,11 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
           const bool flag = valid && !isbad && A > 0.f && !(fabsf(y) > A * xm);
           int bit = y > 0.f ? 1 : 0;
           if (__any_sync(0xffffffffu, flag)) {
-            if (flag) {
-              const uint32_t *P = E + sg.x;
-              const double y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
+            if (!queue_bin(p, flag, row, t, l, bit, lane) && flag) {
+              const EntT *P = E + sg.x;
+              double y64;
+              if (!bin_exact(P, 4 * qp, P + 4 * qp, 4 * qn, xr, y64))
+                y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
               const int b64 = y64 > 0.0 ? 1 : 0;
               ++nflag;
               nchanged += b64 != bit;
@@ -355,9 +480,11 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
           const bool flag = valid && !isbad && !(dist > M && fabsf(tf) < 4194304.f);
           int code = int(fl);
           if (__any_sync(0xffffffffu, flag)) {
-            if (flag) {
-              const uint32_t *P = E + sg.x;
-              const double y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
+            if (!queue_bin(p, flag, row, t, l, code, lane) && flag) {
+              const EntT *P = E + sg.x;
+              double y64;
+              if (!bin_exact(P, 4 * qp, P + 4 * qp, 4 * qn, xr, y64))
+                y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
               const double t1 = __dmul_rn(p.sqrtm, y64);
               const double t2 = __dadd_rn(t1, p.b64[int64_t(t) * m + l]);
               const double t3 = __ddiv_rn(t2, p.w);
@@ -449,6 +576,9 @@ int num_sms() {
 
 int align16(int v) { return (v + 15) & ~15; }
 
+// Entry width: 16-bit byte offsets while 4 (d + 1) fits, else 32-bit.
+int entry_bytes(int d) { return 4 * (d + 1) < 65536 ? 2 : 4; }
+
 Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   Plan best{};
   best.smem = -1;
@@ -478,7 +608,7 @@ Plan make_plan(int d, int m, int L, int cap, int64_t n) {
         const int R = RG * kWarp;
         int off = 0;
         pl.off_ent = off;
-        off = align16(off + Lgb * cap * 4);
+        off = align16(off + Lgb * cap * entry_bytes(d));
         pl.off_seg = off;
         off = align16(off + Lgb * m * 8);
         pl.off_cst = off;
@@ -501,14 +631,19 @@ Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   return best;
 }
 
+template <bool SRP, int DT, typename EntT>
+cudaError_t launch_e(const Args &a, cudaStream_t stream) {
+  const dim3 grid((unsigned)(a.slots * a.pl.G)), block((unsigned)(a.pl.W * kWarp));
+  cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<SRP, DT, EntT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+  if (e != cudaSuccess) return e;
+  sketch_dense_kernel<SRP, DT, EntT><<<grid, block, a.pl.smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <bool SRP, int DT>
 cudaError_t launch_t(const Args &a, cudaStream_t stream) {
-  const dim3 grid((unsigned)(a.slots * a.pl.G)), block((unsigned)(a.pl.W * kWarp));
-  cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<SRP, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       a.pl.smem);
-  if (e != cudaSuccess) return e;
-  sketch_dense_kernel<SRP, DT><<<grid, block, a.pl.smem, stream>>>(a);
-  return cudaGetLastError();
+  return entry_bytes(a.p.d) == 2 ? launch_e<SRP, DT, uint16_t>(a, stream) : launch_e<SRP, DT, uint32_t>(a, stream);
 }
 
 }  // namespace
@@ -526,6 +661,153 @@ SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype) {
   sp.smem = pl.smem;
   sp.ctas = num_sms();
   return sp;
+}
+
+int64_t sketch_queue_cap(int64_t n, int32_t L, int32_t m) {
+  // about 16x the flag rate seen on Gaussian-mixture rows; the excess is rechecked in place
+  return std::min<int64_t>(n * L * m / 256 + 65536, int64_t(1) << 28);
+}
+
+namespace {
+
+template <int DT>
+__device__ __forceinline__ uint32_t x_bits(const void *X, int64_t idx) {
+  return __float_as_uint(load_x<DT>(X, idx));
+}
+
+// One queued bin per thread: the exact FP64 value of the bin (int64 sum on
+// the least exponent grid of its terms, else the ascending FP64 loop over the
+// merged member lists -- the oracle's order), the oracle's code, and the
+// patch of code, bits and key where the fast code was wrong.  E2LSH and
+// multi-word SRP keys are sums mod 2^32 in both halves; one-word SRP keys are
+// the bits themselves.
+template <bool SRP, int DT>
+__global__ void __launch_bounds__(256) sketch_recheck_kernel(const SketchLaunch p, const uint16_t *mlist,
+                                                             const uint32_t *mseg) {
+  const int64_t cnt = min(int64_t(*p.qcount), int64_t(p.qcap));
+  int nflag = 0, nchanged = 0, novf = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x) {
+    const int4 r = p.queue[i];
+    const int64_t row = r.x;
+    const int t = r.y, l = r.z;
+    const int64_t tl = int64_t(t) * p.m + l;
+    const uint32_t start = mseg[2 * tl], np = mseg[2 * tl + 1] & 0xFFFFu, nn = mseg[2 * tl + 1] >> 16;
+    const uint16_t *P = mlist + int64_t(t) * p.d + start;
+    const uint16_t *N = P + np;
+    const int64_t xb = row * p.ld;
+    // exact path
+    int emin = 1 << 20, emax = -(1 << 20);
+    for (uint32_t k = 0; k < np + nn; ++k) {
+      const uint32_t v = x_bits<DT>(p.X, xb + P[k]);
+      if (v & 0x7FFFFFFFu) {
+        const int e = int((v >> 23) & 0xFF);
+        const int E = max(e, 1) - 150;
+        emin = min(emin, E);
+        emax = max(emax, E);
+      }
+    }
+    double y64 = 0.0;
+    bool exact = true;
+    if (emax >= emin) {
+      exact = emax - emin <= 29;
+      if (exact) {
+        constexpr unsigned long long kCap = 1ull << 53;
+        unsigned long long sum = 0, mag = 0;
+        for (uint32_t k = 0; k < np + nn; ++k) {
+          const uint32_t v = x_bits<DT>(p.X, xb + P[k]);
+          const int e = int((v >> 23) & 0xFF);
+          const uint32_t M = (v & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+          const unsigned long long tv = (unsigned long long)M << max(max(e, 1) - 150 - emin, 0);
+          sum += ((v >> 31) ^ (k >= np ? 1u : 0u)) ? 0ull - tv : tv;
+          mag = min(mag + tv, kCap);
+        }
+        exact = mag < kCap;
+        if (exact) y64 = ldexp(double((long long)sum), emin);
+      }
+    }
+    if (!exact) {
+      // the sequential loop in ascending j over the merged halves
+      uint32_t ip = 0, in = 0;
+      y64 = 0.0;
+      while (ip < np || in < nn) {
+        const uint32_t jp = ip < np ? P[ip] : 0xFFFFFFFFu, jn = in < nn ? N[in] : 0xFFFFFFFFu;
+        if (jp < jn) {
+          y64 = __dadd_rn(y64, double(__uint_as_float(x_bits<DT>(p.X, xb + jp))));
+          ++ip;
+        } else {
+          y64 = __dadd_rn(y64, -double(__uint_as_float(x_bits<DT>(p.X, xb + jn))));
+          ++in;
+        }
+      }
+    }
+    int c64;
+    if (SRP) {
+      c64 = y64 > 0.0 ? 1 : 0;
+    } else {
+      const double f = floor(__ddiv_rn(__dadd_rn(__dmul_rn(p.sqrtm, y64), p.b64[tl]), p.w));
+      if (f >= -2147483648.0 && f <= 2147483647.0) {
+        c64 = int(f);
+      } else {
+        c64 = INT32_MIN;
+        ++novf;
+      }
+    }
+    ++nflag;
+    if (c64 == r.w) continue;
+    ++nchanged;
+    uint64_t *key = p.keys ? p.keys + int64_t(t) * p.key_ld + row : nullptr;
+    if (SRP) {
+      const int words = (p.m + 63) >> 6;
+      if (p.bits)
+        atomicXor(reinterpret_cast<unsigned long long *>(p.bits + (row * p.L + t) * words + (l >> 6)), 1ull << (l & 63));
+      if (key) {
+        if (p.m <= 64) {
+          atomicXor(reinterpret_cast<unsigned long long *>(key), 1ull << l);
+        } else {
+          const uint32_t sgn = c64 ? 1u : 0xFFFFFFFFu;  // +1 or -1 mod 2^32
+          atomicAdd(reinterpret_cast<unsigned int *>(key) + 1, sgn * p.ka[tl]);
+          atomicAdd(reinterpret_cast<unsigned int *>(key), sgn * p.kb[tl]);
+        }
+      }
+    } else {
+      if (p.codes) p.codes[(row * p.L + t) * p.m + l] = c64;
+      const uint32_t dc = uint32_t(c64) - uint32_t(r.w);
+      if (key) {
+        atomicAdd(reinterpret_cast<unsigned int *>(key) + 1, dc * p.ka[tl]);
+        atomicAdd(reinterpret_cast<unsigned int *>(key), dc * p.kb[tl]);
+      }
+    }
+  }
+  if (p.counters) {
+    if (nflag) atomicAdd(p.counters + CNT_FLAGGED, (unsigned long long)nflag);
+    if (nchanged) atomicAdd(p.counters + CNT_CHANGED, (unsigned long long)nchanged);
+    if (novf) atomicAdd(p.counters + CNT_OVERFLOW, (unsigned long long)novf);
+  }
+  if (novf) atomicOr(p.status, STATUS_OVERFLOW);
+}
+
+template <bool SRP, int DT>
+cudaError_t launch_recheck_t(const SketchLaunch &p, const uint16_t *mlist, const uint32_t *mseg,
+                             cudaStream_t stream) {
+  sketch_recheck_kernel<SRP, DT><<<unsigned(num_sms()) * 8, 256, 0, stream>>>(p, mlist, mseg);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_recheck(const SketchLaunch &p, const uint16_t *mlist, const uint32_t *mseg,
+                                  cudaStream_t stream) {
+  if (p.n <= 0 || !p.queue) return cudaSuccess;
+  const bool srp = kind_is_srp(p.kind);
+  switch (p.dtype) {
+    case LSH_F32: return srp ? launch_recheck_t<true, LSH_F32>(p, mlist, mseg, stream)
+                             : launch_recheck_t<false, LSH_F32>(p, mlist, mseg, stream);
+    case LSH_BF16: return srp ? launch_recheck_t<true, LSH_BF16>(p, mlist, mseg, stream)
+                              : launch_recheck_t<false, LSH_BF16>(p, mlist, mseg, stream);
+    case LSH_F16: return srp ? launch_recheck_t<true, LSH_F16>(p, mlist, mseg, stream)
+                             : launch_recheck_t<false, LSH_F16>(p, mlist, mseg, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {

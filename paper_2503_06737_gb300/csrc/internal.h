@@ -89,6 +89,8 @@ struct lsh_family_s {
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
   uint16_t *d_colmajor = nullptr; // CS kinds: [d][L] bin | neg << 15 (CSR path)
+  uint16_t *d_mlist = nullptr;    // CS/HCS, d < 65536: [L][d] coordinates by (bin, sign, j)
+  uint32_t *d_mseg = nullptr;     // [L][m][2]: start in the table's list, n(+) | n(-) << 16
 };
 
 struct lsh_index_s {
@@ -135,10 +137,20 @@ struct SketchLaunch {
   float *proj;           // [n][L][m]
   unsigned long long *counters;  // CNT_NUM or nullptr
   uint32_t *status;
+  // deferred recheck (dense-row sketch kernel): flagged bins {row, t, l, fast code}
+  int4 *queue = nullptr;
+  uint32_t *qcount = nullptr;
+  uint32_t qcap = 0;
 };
 
-// Dense-row CS/HCS hashing (all L tables, one launch).
+// Dense-row CS/HCS hashing (all L tables, one launch).  With p.queue set,
+// bins within the error bound are queued instead of rechecked in place;
+// launch_sketch_recheck then computes their exact values from the member
+// lists and patches codes, bits and keys.
 cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream);
+cudaError_t launch_sketch_recheck(const SketchLaunch &p, const uint16_t *mlist, const uint32_t *mseg,
+                                  cudaStream_t stream);
+int64_t sketch_queue_cap(int64_t n, int32_t L, int32_t m);
 // Plan of the dense-row kernel for a shape (for reporting / autotuning).
 struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
 SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);

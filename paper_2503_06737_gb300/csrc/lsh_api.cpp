@@ -85,6 +85,8 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_Gint);
   cudaFree(f->d_status);
   cudaFree(f->d_colmajor);
+  cudaFree(f->d_mlist);
+  cudaFree(f->d_mseg);
   delete f;
 }
 
@@ -180,8 +182,22 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
   if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs
     LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
-  LSH_CUDA_TRY(launch_sketch_dense(p, stream));
-  count_launches(1);
+  // large batches defer their boundary rechecks to a second kernel (queue
+  // from the stream-ordered pool); small ones recheck in place and allocate nothing
+  void *qbuf = nullptr;
+  if (f->d_mlist && X->n >= 4096) {
+    const int64_t qcap = sketch_queue_cap(X->n, d.L, d.m);
+    LSH_CUDA_TRY(cudaMallocAsync(&qbuf, size_t(16 + 16 * qcap), stream));
+    p.qcount = static_cast<uint32_t *>(qbuf);
+    p.queue = reinterpret_cast<int4 *>(static_cast<char *>(qbuf) + 16);
+    p.qcap = uint32_t(qcap);
+    LSH_CUDA_TRY(cudaMemsetAsync(qbuf, 0, 16, stream));
+  }
+  cudaError_t e = launch_sketch_dense(p, stream);
+  if (e == cudaSuccess && qbuf) e = launch_sketch_recheck(p, f->d_mlist, f->d_mseg, stream);
+  if (qbuf) cudaFreeAsync(qbuf, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dense-row sketch hash");
+  count_launches(qbuf ? 2 : 1);
   return LSH_OK;
 }
 
@@ -342,6 +358,43 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
         cm[size_t(j) * d.L + t] = uint16_t(h.bins[src] | (h.signs[src] < 0 ? 0x8000 : 0));
       }
     e = upload(&f->d_colmajor, cm.data(), cm.size());
+  }
+  if (e == cudaSuccess && kind_is_sketch(d.kind) && d.d < 65536) {
+    // per-table member lists for the deferred recheck: the coordinates of each
+    // bin with s = +1 in ascending j, then those with s = -1
+    std::vector<uint16_t> ml(size_t(d.L) * d.d);
+    std::vector<uint32_t> ms(size_t(d.L) * d.m * 2);
+    std::vector<int> bin(d.d), neg(d.d);
+    std::vector<uint32_t> cnt(size_t(2) * d.m), cur(size_t(2) * d.m);
+    for (int t = 0; t < d.L; ++t) {
+      std::fill(cnt.begin(), cnt.end(), 0u);
+      for (int j = 0; j < d.d; ++j) {
+        int r = j, off = 0, stride = 1, bn = 0, ng = 0;
+        for (int k = 0; k < d.N; ++k) {
+          const int ik = r % d.dims[k];
+          r /= d.dims[k];
+          const size_t src = size_t(t) * h.dsum + off + ik;
+          bn += h.bins[src] * stride;
+          ng ^= h.signs[src] < 0 ? 1 : 0;
+          stride *= d.mdims[k];
+          off += d.dims[k];
+        }
+        bin[j] = bn;
+        neg[j] = ng;
+        ++cnt[size_t(2) * bn + ng];
+      }
+      uint32_t start = 0;
+      for (int l = 0; l < d.m; ++l) {
+        ms[(size_t(t) * d.m + l) * 2] = start;
+        ms[(size_t(t) * d.m + l) * 2 + 1] = cnt[2 * l] | (cnt[2 * l + 1] << 16);
+        cur[2 * l] = start;
+        cur[2 * l + 1] = start + cnt[2 * l];
+        start += cnt[2 * l] + cnt[2 * l + 1];
+      }
+      for (int j = 0; j < d.d; ++j) ml[size_t(t) * d.d + cur[size_t(2) * bin[j] + neg[j]]++] = uint16_t(j);
+    }
+    e = upload(&f->d_mlist, ml.data(), ml.size());
+    if (e == cudaSuccess) e = upload(&f->d_mseg, ms.data(), ms.size());
   }
   if (e == cudaSuccess) e = cudaMalloc(&f->d_status, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(f->d_status, 0, sizeof(uint32_t));

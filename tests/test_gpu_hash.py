@@ -160,3 +160,50 @@ def test_full_size_gist_like_sampled(kind):
     assert stats["n_entries"] == wl["n"] * 50 * 64
     del X
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind,d,m,L,dims,mdims,dtype", [
+    ("cs_e2lsh", 128, 16, 8, None, None, torch.float32),
+    ("hcs_e2lsh", 128, 16, 8, [8, 16], [4, 4], torch.bfloat16),
+    ("cs_srp", 128, 16, 8, None, None, torch.float32),
+    ("hcs_srp", 128, 16, 8, [8, 16], [4, 4], torch.float16),
+    ("cs_srp", 100, 256, 3, None, None, torch.float32),     # multi-word SRP keys patched by sums
+])
+def test_deferred_recheck_patches(kind, d, m, L, dims, mdims, dtype):
+    """Batches of 4096 rows or more queue their boundary bins for the recheck
+    kernel, which patches codes, bits and keys; narrow bins (and SRP rows
+    built to cancel) make many of them change."""
+    X = _rows(6000, d, seed=31, dtype=dtype)
+    w = 0.02 if "e2lsh" in kind else 4.0
+    if "srp" in kind:
+        X = torch.round(X * 1.5)  # small integers: many bins sum to exactly zero
+    stats, _ = compare_hash(dict(kind=kind, d=d, m=m, L=L, w=w, seed=17, dims=dims, mdims=mdims), X)
+    assert stats["n_flagged"] > 0
+
+
+def test_deferred_recheck_repairs_cancellation():
+    """The exact-cancellation rows of test_cancellation_repaired_by_recheck, in a
+    batch large enough to take the queue: the patches must restore the bits."""
+    d, m, L = 256, 8, 4
+    fam_args = dict(kind="cs_srp", d=d, m=m, L=L, seed=21)
+    tabs = lsh.sample_family_tables(**fam_args)
+    rng = np.random.default_rng(1)
+    X = (rng.standard_normal((6000, d)) * 1e-3).astype(np.float32)
+    h, s = tabs["bins"][0], tabs["signs"][0]
+    for l in range(m):
+        members = np.flatnonzero(h == l)
+        pos = [j for j in members if s[j] > 0]
+        neg = [j for j in members if s[j] < 0]
+        if pos and neg:
+            X[:, max(pos)] = 1e8
+            X[:, max(neg)] = 1e8
+    stats, _ = compare_hash(fam_args, torch.from_numpy(X).cuda(), check_proj=False)
+    assert stats["n_changed"] > 0
+
+
+def test_deferred_recheck_queue_overflow():
+    """Bins far narrower than the error bound flag nearly every entry: more
+    than the queue holds, so the rest is rechecked inside the main kernel."""
+    X = _rows(5000, 128, seed=32)
+    stats, _ = compare_hash(dict(kind="cs_e2lsh", d=128, m=16, L=8, w=1e-5, seed=18), X)
+    assert stats["n_flagged"] > 0.9 * 5000 * 128
