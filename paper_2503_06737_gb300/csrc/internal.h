@@ -178,10 +178,16 @@ size_t tc_dense_scratch_bytes(int64_t n, int64_t ML);
 cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
                             const int32_t *Gint, void *scratch, cudaStream_t stream);
 
-// Query path: probe + dedup + exact top-k rerank, one CTA per query.
+// Query path: probe + dedup + exact top-k rerank, G CTAs per query
+// (query_split: more CTAs per query for small batches) whose lists the last
+// CTA merges.  scratch: query_scratch_bytes(scratch_q, k) bytes, its first
+// scratch_q words zero (the kernel leaves them zero); NULL means G = 1.
+int query_split(int64_t q, int32_t k);
+size_t query_scratch_bytes(int64_t q_max, int32_t k);
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
                          const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
-                         float *out_dist, unsigned long long *counters, cudaStream_t stream);
+                         float *out_dist, unsigned long long *counters, void *scratch, int64_t scratch_q,
+                         cudaStream_t stream);
 
 // Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
 // Allocates its temporaries with cudaMallocAsync on `stream`.

@@ -182,10 +182,11 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
   if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs
     LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
-  // large batches defer their boundary rechecks to a second kernel (queue
-  // from the stream-ordered pool); small ones recheck in place and allocate nothing
+  // large batches (8192 rows or more) defer their boundary rechecks to a
+  // second kernel (queue from the stream-ordered pool); smaller ones (query
+  // batches among them) recheck in place and allocate nothing
   void *qbuf = nullptr;
-  if (f->d_mlist && X->n >= 4096) {
+  if (f->d_mlist && X->n >= 8192) {
     const int64_t qcap = sketch_queue_cap(X->n, d.L, d.m);
     LSH_CUDA_TRY(cudaMallocAsync(&qbuf, size_t(16 + 16 * qcap), stream));
     p.qcount = static_cast<uint32_t *>(qbuf);
@@ -601,8 +602,10 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
   keep_pool_warm();
   uint64_t *qkeys = nullptr;
   unsigned long long *cnt = nullptr;
+  void *qscratch = nullptr;
   LSH_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&qkeys), sizeof(uint64_t) * size_t(q) * d.L, stream));
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaMallocAsync(&qscratch, query_scratch_bytes(q, k), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(qscratch, 0, size_t(q) * 4, stream);
   if (stats) {
     e = cudaMallocAsync(reinterpret_cast<void **>(&cnt), 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), stream);
@@ -611,7 +614,7 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
   else st = cuda_fail(e, "lsh_query temporaries");
   if (st == LSH_OK && idx->n > 0) {
     e = launch_query(qkeys, q, d.L, k, kind_is_srp(d.kind) ? 1 : 0, d.d, Q->values, Q->dtype, Q->ld, idx, ids,
-                     dist, cnt, stream);
+                     dist, cnt, qscratch, q, stream);
     if (e != cudaSuccess) st = cuda_fail(e, "lsh_query launch");
     else count_launches(1);
   } else if (st == LSH_OK) {
@@ -629,6 +632,7 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
     if (e != cudaSuccess) st = cuda_fail(e, "lsh_query stats");
   }
   cudaFreeAsync(qkeys, stream);
+  if (qscratch) cudaFreeAsync(qscratch, stream);
   if (cnt) cudaFreeAsync(cnt, stream);
   if (stats && st == LSH_OK) {
     e = cudaStreamSynchronize(stream);

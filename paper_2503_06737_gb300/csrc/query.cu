@@ -9,13 +9,16 @@
 //   gather  the union, flattened over tables, is processed in chunks of up
 //           to kCap ids staged in shared memory;
 //   dedup   each chunk is bitonic-sorted and compacted to distinct ids;
-//   rerank  one warp per candidate: FP32 distance from the index's copy of
-//           the data row (Euclidean for E2LSH kinds, 1 - cos for SRP kinds);
+//   rerank  one thread per candidate: FP32 distance from the index's copy of
+//           the data row, read with independent 16-byte loads (Euclidean for
+//           E2LSH kinds, 1 - cos for SRP kinds);
 //   top-k   merged into a running (distance, id) list.  An id that repeats in
 //           a later chunk has the same distance: if it is in the list it is
 //           skipped, and if it is not, it lost against a list that has only
 //           improved since, so it cannot enter -- the union is deduplicated
 //           exactly without a global sort.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,9 +48,17 @@ struct QueryArgs {
   const void *X;
   int32_t x_dtype;
   int64_t x_ld;
+  int32_t vec16;           // rows 16-byte aligned and d a multiple of the elements per 16 bytes
   int32_t *out_ids;
   float *out_dist;
-  unsigned long long *counters;  // [4]: candidates, unique, max unique (atomicMax), queries
+  unsigned long long *counters;  // [4]: candidates, unique, max unique per CTA (atomicMax), queries
+  // split queries: G CTAs per query, each a share of the chunks; partial
+  // lists pd/pi [q][G][k]; done[q] counts finished CTAs (the last merges and
+  // resets it to 0)
+  int32_t G;
+  float *pd;
+  uint32_t *pi;
+  uint32_t *done;
 };
 
 __device__ __forceinline__ float ld_elem(const void *p, int dtype, int64_t idx) {
@@ -76,7 +87,8 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
   __shared__ int red_s[kThreads / 32];
   __shared__ float qnorm2;
 
-  const int64_t qi = blockIdx.x;
+  const int64_t qi = blockIdx.x / a.G;
+  const int g = int(blockIdx.x % a.G);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int L = a.L, k = a.k, d = a.d;
 
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
   const uint32_t C = pre[L];
   uint32_t uniq_total = 0, uniq_max = 0;
 
-  for (uint32_t c0 = 0; c0 < C; c0 += kCap) {
+  for (uint32_t c0 = uint32_t(g) * kCap; c0 < C; c0 += uint32_t(a.G) * kCap) {
     const uint32_t cc = min(uint32_t(kCap), C - c0);
     uint32_t P = 1;
     while (P < cc) P <<= 1;
@@ -195,35 +207,78 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
     __syncthreads();
     uniq_total += U;
     uniq_max = max(uniq_max, U);
-    // distances: one warp per candidate
-    for (uint32_t u = warp; u < U; u += kThreads / 32) {
+    // distances: one thread per candidate, its row read with independent
+    // 16-byte loads (many rows in flight per SM), the query from shared memory
+    for (uint32_t u = tid; u < U; u += kThreads) {
       const uint32_t id = cand[u];
       const int64_t base = int64_t(id) * a.x_ld;
       float acc = 0.f, xx = 0.f;
-      for (int j = lane; j < d; j += 32) {
-        const float x = ld_elem(a.X, a.x_dtype, base + j);
-        if (a.metric == 0) {
-          const float e = qv[j] - x;
-          acc = fmaf(e, e, acc);
-        } else {
-          acc = fmaf(qv[j], x, acc);
-          xx = fmaf(x, x, xx);
-        }
-      }
+      if (a.vec16) {
+        // rows are 16-byte aligned: eight 2-byte or four 4-byte elements a load
+        const uint4 *xr = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(a.X) +
+                                                          base * (a.x_dtype == LSH_F32 ? 4 : 2));
+        const int per = a.x_dtype == LSH_F32 ? 4 : 8;
+        const int nv = d / per;
+        for (int v0 = 0; v0 < nv; v0 += 8) {
+          uint4 w[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        xx += __shfl_xor_sync(0xffffffffu, xx, o);
-      }
-      if (lane == 0) {
-        float dist;
-        if (a.metric == 0) {
-          dist = sqrtf(acc);
-        } else {
-          dist = (qnorm2 > 0.f && xx > 0.f) ? 1.f - acc / (sqrtf(qnorm2) * sqrtf(xx)) : 1.f;
+          for (int t = 0; t < 8; ++t) w[t] = v0 + t < nv ? __ldg(xr + v0 + t) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            if (v0 + t >= nv) break;
+            float x[8];
+            const uint32_t ww[4] = {w[t].x, w[t].y, w[t].z, w[t].w};
+            if (a.x_dtype == LSH_F32) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) x[e] = __uint_as_float(ww[e]);
+            } else if (a.x_dtype == LSH_BF16) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                x[2 * e] = __uint_as_float(ww[e] << 16);
+                x[2 * e + 1] = __uint_as_float(ww[e] & 0xFFFF0000u);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&ww[e]));
+                x[2 * e] = f.x;
+                x[2 * e + 1] = f.y;
+              }
+            }
+            const int j0 = (v0 + t) * per;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              if (e >= per) break;
+              const float qj = qv[j0 + e];
+              if (a.metric == 0) {
+                const float df = qj - x[e];
+                acc = fmaf(df, df, acc);
+              } else {
+                acc = fmaf(qj, x[e], acc);
+                xx = fmaf(x[e], x[e], xx);
+              }
+            }
+          }
         }
-        cdist[u] = dist;
+      } else {
+        for (int j = 0; j < d; ++j) {
+          const float x = ld_elem(a.X, a.x_dtype, base + j);
+          if (a.metric == 0) {
+            const float df = qv[j] - x;
+            acc = fmaf(df, df, acc);
+          } else {
+            acc = fmaf(qv[j], x, acc);
+            xx = fmaf(x, x, xx);
+          }
+        }
       }
+      float dist;
+      if (a.metric == 0) {
+        dist = sqrtf(acc);
+      } else {
+        dist = (qnorm2 > 0.f && xx > 0.f) ? 1.f - acc / (sqrtf(qnorm2) * sqrtf(xx)) : 1.f;
+      }
+      cdist[u] = dist;
     }
     __syncthreads();
     // drop candidates already in the top-k list (same id => same distance)
@@ -301,24 +356,118 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
       __syncthreads();
     }
   }
+  if (tid == 0 && a.counters) {
+    if (g == 0) atomicAdd(a.counters + 0, (unsigned long long)C);
+    atomicAdd(a.counters + 1, (unsigned long long)uniq_total);
+    atomicMax(a.counters + 2, (unsigned long long)uniq_max);
+    if (g == 0) atomicAdd(a.counters + 3, 1ull);
+  }
+  if (a.G > 1) {
+    // hand this CTA's list over; the last CTA of the query merges all G lists
+    __shared__ int s_last;
+    const int64_t pb = (qi * a.G + g) * k;
+    for (int r = tid; r < k; r += kThreads) {
+      a.pd[pb + r] = topd[r];
+      a.pi[pb + r] = topi[r];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(a.done + qi, 1u) == uint32_t(a.G - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int U = a.G * k;  // <= kCap (launch_query bounds G)
+    for (int u = tid; u < U; u += kThreads) {
+      cand[u] = __ldcg(a.pi + qi * a.G * k + u);
+      cdist[u] = __ldcg(a.pd + qi * a.G * k + u);
+    }
+    __shared__ uint32_t s_win;
+    __syncthreads();
+    // k rounds of block argmin over the G lists; an id in several lists has
+    // the same distance in each, so every copy of the winner is retired
+    for (int r = 0; r < k; ++r) {
+      float bd = __int_as_float(0x7f800000);
+      uint32_t bi = 0xffffffffu;
+      for (int u = tid; u < U; u += kThreads)
+        if (cand[u] != 0xffffffffu && better(cdist[u], cand[u], bd, bi)) {
+          bd = cdist[u];
+          bi = cand[u];
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(od, oi, bd, bi)) {
+          bd = od;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        red_d[warp] = bd;
+        red_i[warp] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float fd = red_d[0];
+        uint32_t fi = red_i[0];
+        for (int w = 1; w < kThreads / 32; ++w)
+          if (better(red_d[w], red_i[w], fd, fi)) {
+            fd = red_d[w];
+            fi = red_i[w];
+          }
+        topd[r] = fd;
+        topi[r] = fi;
+        s_win = fi;
+      }
+      __syncthreads();
+      const uint32_t win = s_win;
+      if (win != 0xffffffffu)
+        for (int u = tid; u < U; u += kThreads)
+          if (cand[u] == win) cand[u] = 0xffffffffu;
+      __syncthreads();
+    }
+    if (tid == 0) a.done[qi] = 0;  // ready for the next launch on this scratch
+  }
   for (int r = tid; r < k; r += kThreads) {
     const bool ok = topi[r] != 0xffffffffu;
     a.out_ids[qi * k + r] = ok ? int32_t(topi[r]) : -1;
     a.out_dist[qi * k + r] = ok ? topd[r] : __int_as_float(0x7f800000);
   }
-  if (tid == 0 && a.counters) {
-    atomicAdd(a.counters + 0, (unsigned long long)C);
-    atomicAdd(a.counters + 1, (unsigned long long)uniq_total);
-    atomicMax(a.counters + 2, (unsigned long long)uniq_max);
-    atomicAdd(a.counters + 3, 1ull);
-  }
 }
 
 }  // namespace
 
+namespace {
+int num_sms_q() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+int64_t align16(int64_t b) { return (b + 15) & ~int64_t(15); }
+}  // namespace
+
+int query_split(int64_t q, int32_t k) {
+  // enough CTAs for the SMs (four each); at most 32 per query and G k <= kCap
+  const int64_t target = int64_t(num_sms_q()) * 4;
+  int64_t G = q > 0 ? target / q : 1;
+  G = std::max<int64_t>(1, std::min<int64_t>(G, std::min<int64_t>(32, kCap / std::max(k, 1))));
+  return int(G);
+}
+
+size_t query_scratch_bytes(int64_t q_max, int32_t k) {
+  const int64_t lists = std::max<int64_t>(q_max, int64_t(num_sms_q()) * 4 + 32) * k;
+  return size_t(align16(q_max * 4) + 2 * align16(lists * 4));
+}
+
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
                          const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
-                         float *out_dist, unsigned long long *counters, cudaStream_t stream) {
+                         float *out_dist, unsigned long long *counters, void *scratch, int64_t scratch_q,
+                         cudaStream_t stream) {
   if (q <= 0) return cudaSuccess;
   if (L > kMaxL || k > kMaxK) return cudaErrorInvalidValue;
   QueryArgs a{};
@@ -339,15 +488,29 @@ cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k,
   a.X = idx->d_data;
   a.x_dtype = idx->data_dtype;
   a.x_ld = idx->data_ld;
+  {
+    const int64_t es = idx->data_dtype == LSH_F32 ? 4 : 2;
+    a.vec16 = (d % (16 / es) == 0) && (a.x_ld * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
+  }
   a.out_ids = out_ids;
   a.out_dist = out_dist;
   a.counters = counters;
+  a.G = scratch && q <= scratch_q ? query_split(q, k) : 1;
+  if (a.G > 1) {
+    // layout of query_scratch_bytes(scratch_q, k): done[scratch_q], then the two list arrays
+    char *sb = static_cast<char *>(scratch);
+    const int64_t lists = std::max<int64_t>(scratch_q, int64_t(num_sms_q()) * 4 + 32) * k;
+    a.done = reinterpret_cast<uint32_t *>(sb);
+    a.pd = reinterpret_cast<float *>(sb + align16(scratch_q * 4));
+    a.pi = reinterpret_cast<uint32_t *>(sb + align16(scratch_q * 4) + align16(lists * 4));
+    if (q * a.G * k > lists) a.G = 1;
+  }
   const int smem = d * 4 + (2 * kMaxL + 1) * 4 + kCap * 8 + kMaxK * 8;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (q > INT32_MAX) return cudaErrorInvalidValue;
-  query_kernel<<<(unsigned)q, kThreads, smem, stream>>>(a);
+  if (q * a.G > INT32_MAX) return cudaErrorInvalidValue;
+  query_kernel<<<(unsigned)(q * a.G), kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

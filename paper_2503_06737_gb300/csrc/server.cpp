@@ -53,6 +53,7 @@ struct Slot {
   uint64_t *qkeys = nullptr;     // [L][max_batch]
   int32_t *ids_d = nullptr;      // [max_batch][k]
   float *dist_d = nullptr;
+  void *qscratch = nullptr;      // split-query lists (query_scratch_bytes(max_batch, k))
   unsigned char *Qh = nullptr;   // pinned staging
   int32_t *ids_h = nullptr;
   float *dist_h = nullptr;
@@ -130,7 +131,7 @@ lsh_status enqueue_batch(lsh_server_s *s, Slot &sl, int64_t rows, int32_t dtype)
   lsh_status st = hash_impl(s->idx->fam, &Q, nullptr, sl.qkeys, rows, nullptr, nullptr, sl.stream);
   if (st != LSH_OK) return st;
   LSH_CUDA_TRY(launch_query(sl.qkeys, rows, d.L, s->cfg.k, kind_is_srp(d.kind) ? 1 : 0, d.d, sl.Qd, dtype, d.d,
-                            s->idx, sl.ids_d, sl.dist_d, nullptr, sl.stream));
+                            s->idx, sl.ids_d, sl.dist_d, nullptr, sl.qscratch, s->cfg.max_batch, sl.stream));
   if (!s->cfg.use_graphs) count_launches(1);
   LSH_CUDA_TRY(cudaMemcpyAsync(sl.ids_h, sl.ids_d, size_t(rows) * s->cfg.k * 4, cudaMemcpyDeviceToHost, sl.stream));
   LSH_CUDA_TRY(cudaMemcpyAsync(sl.dist_h, sl.dist_d, size_t(rows) * s->cfg.k * 4, cudaMemcpyDeviceToHost,
@@ -262,6 +263,7 @@ void free_server(lsh_server_s *s) {
     cudaFree(sl.qkeys);
     cudaFree(sl.ids_d);
     cudaFree(sl.dist_d);
+    cudaFree(sl.qscratch);
     cudaFreeHost(sl.Qh);
     cudaFreeHost(sl.ids_h);
     cudaFreeHost(sl.dist_h);
@@ -306,6 +308,8 @@ lsh_status lsh_server_create(lsh_index_t idx, const lsh_server_config *cfg, lsh_
     if (e == cudaSuccess) e = cudaMalloc(&sl.qkeys, mb * d.L * 8);
     if (e == cudaSuccess) e = cudaMalloc(&sl.ids_d, mb * cfg->k * 4);
     if (e == cudaSuccess) e = cudaMalloc(&sl.dist_d, mb * cfg->k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.qscratch, query_scratch_bytes(cfg->max_batch, cfg->k));
+    if (e == cudaSuccess) e = cudaMemset(sl.qscratch, 0, mb * 4);  // the per-query counters start at zero
     if (e == cudaSuccess) e = cudaMallocHost(&sl.Qh, mb * d.d * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.ids_h, mb * cfg->k * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.dist_h, mb * cfg->k * 4);

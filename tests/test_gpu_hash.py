@@ -170,10 +170,10 @@ def test_full_size_gist_like_sampled(kind):
     ("cs_srp", 100, 256, 3, None, None, torch.float32),     # multi-word SRP keys patched by sums
 ])
 def test_deferred_recheck_patches(kind, d, m, L, dims, mdims, dtype):
-    """Batches of 4096 rows or more queue their boundary bins for the recheck
+    """Batches of 8192 rows or more queue their boundary bins for the recheck
     kernel, which patches codes, bits and keys; narrow bins (and SRP rows
     built to cancel) make many of them change."""
-    X = _rows(6000, d, seed=31, dtype=dtype)
+    X = _rows(9000, d, seed=31, dtype=dtype)
     w = 0.02 if "e2lsh" in kind else 4.0
     if "srp" in kind:
         X = torch.round(X * 1.5)  # small integers: many bins sum to exactly zero
@@ -188,7 +188,7 @@ def test_deferred_recheck_repairs_cancellation():
     fam_args = dict(kind="cs_srp", d=d, m=m, L=L, seed=21)
     tabs = lsh.sample_family_tables(**fam_args)
     rng = np.random.default_rng(1)
-    X = (rng.standard_normal((6000, d)) * 1e-3).astype(np.float32)
+    X = (rng.standard_normal((9000, d)) * 1e-3).astype(np.float32)
     h, s = tabs["bins"][0], tabs["signs"][0]
     for l in range(m):
         members = np.flatnonzero(h == l)
@@ -204,6 +204,6 @@ def test_deferred_recheck_repairs_cancellation():
 def test_deferred_recheck_queue_overflow():
     """Bins far narrower than the error bound flag nearly every entry: more
     than the queue holds, so the rest is rechecked inside the main kernel."""
-    X = _rows(5000, 128, seed=32)
+    X = _rows(9000, 128, seed=32)
     stats, _ = compare_hash(dict(kind="cs_e2lsh", d=128, m=16, L=8, w=1e-5, seed=18), X)
-    assert stats["n_flagged"] > 0.9 * 5000 * 128
+    assert stats["n_flagged"] > 0.9 * 9000 * 128

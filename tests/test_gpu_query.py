@@ -123,3 +123,20 @@ def test_query_needs_kept_data():
     idx = fam.build_index(X, keep_data=False)
     with pytest.raises(lsh.LshError):
         idx.query(X[:2], k=3)
+
+
+def test_query_split_over_ctas_is_batch_invariant():
+    """Small batches spread each query over several CTAs whose lists the last
+    one merges (with duplicates across lists); the answer of a query must not
+    depend on the batch it came in, and must pass the oracle check."""
+    X = workloads.gmm(6000, 64, 8, seed=41, device="cpu").cuda()
+    Q, _ = workloads.noisy_queries(X, 700, 0.05, seed=42)
+    args = dict(kind="cs_e2lsh", d=64, m=8, L=12, w=16.0, seed=43)
+    _run(args, X, Q[:3], k=10)
+    fam = lsh.Family(**args)
+    idx = fam.build_index(X, keep_data=True)
+    full = idx.query(Q, k=10)
+    for lo, hi in ((0, 1), (5, 12), (100, 300)):
+        part = idx.query(Q[lo:hi].contiguous(), k=10)
+        assert torch.equal(part["ids"], full["ids"][lo:hi]), (lo, hi)
+        assert torch.equal(part["dist"], full["dist"][lo:hi]), (lo, hi)
