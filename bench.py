@@ -362,7 +362,7 @@ def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
     return out
 
 
-def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=200000.0, seconds_per_load=8.0):
+def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=5e6, seconds_per_load=8.0):
     """Serving workload: 10,000,000 x 128 FP16 points from a 1,024-component
     mixture resident on the GPU; HCS-E2LSH (8 x 16 -> 4 x 4, m = 16) and
     CS-E2LSH (m = 12), L = 32, each with w the smallest value on a grid that

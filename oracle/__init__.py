@@ -106,6 +106,8 @@ def _declare(L):
         getattr(L, nm).argtypes = [ctypes.c_uint16]
     L.orc_from_e4m3.restype = D
     L.orc_from_e4m3.argtypes = [ctypes.c_uint8]
+    L.orc_round_e4m3.restype = D
+    L.orc_round_e4m3.argtypes = [D]
     L.orc_cs_project.restype = None
     L.orc_cs_project.argtypes = [P, I32, P, P, I32, P]
     L.orc_hcs_project.restype = None
@@ -193,7 +195,7 @@ class Family:
 def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32) -> Family:
     """Draw the family (Definitions 2-5) from `seed`.  CS kinds take dims=[d],
     mdims=[m]; HCS kinds take the mode sizes (prod(dims) >= d, prod(mdims) = m).
-    Dense kinds: compute = BF16 rounds every Gaussian entry to bfloat16."""
+    Dense kinds: compute = BF16 (E4M3) rounds every Gaussian entry to bfloat16 (FP8 E4M3)."""
     kind = KIND_NAMES.get(kind, kind)
     lb = lib()
     if is_dense(kind):
@@ -369,6 +371,11 @@ def mix64(z: int) -> int:
 def from_bf16(h): return float(lib().orc_from_bf16(int(h)))
 def from_f16(h): return float(lib().orc_from_f16(int(h)))
 def from_e4m3(q): return float(lib().orc_from_e4m3(int(q)))
+
+
+def round_e4m3(v) -> float:
+    """The nearest FP8 E4M3 value (ties to even, saturating at 448)."""
+    return float(lib().orc_round_e4m3(float(v)))
 
 
 def num_threads() -> int:

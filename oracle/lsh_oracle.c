@@ -130,13 +130,30 @@ static float orc_round_bf16(float f) {
   return f;
 }
 
+/* Round a finite value to the nearest OCP FP8 E4M3 value (3 fraction bits,
+ * exponent bias 7, subnormal quantum 2^-9, largest finite 448), ties to
+ * even; magnitudes above 448 saturate to 448.  Written from the format's
+ * definition: the quantum of |v| in [2^e, 2^(e+1)) is 2^(e-3) for e >= -6. */
+double orc_round_e4m3(double v) {
+  if (v == 0.0 || v != v) return v;
+  double a = fabs(v);
+  int e;
+  frexp(a, &e);          /* a = f 2^e, f in [0.5, 1): a in [2^(e-1), 2^e) */
+  int q = e - 1 - 3;     /* quantum exponent for the normal range */
+  if (e - 1 < -6) q = -9;
+  double r = nearbyint(ldexp(a, -q));  /* default mode: ties to even */
+  double out = ldexp(r, q);
+  if (out > 448.0) out = 448.0;
+  return v < 0 ? -out : out;
+}
+
 /*
  * Dense Gaussian projection family (Definitions 2 and 3: r ~ N(0, I_d)).
  * Per table t: for j = 0..d-1, for l = 0..m-1: two draws r1, r2;
  *   u1 = (hi53(r1) + 1) 2^-53 in (0,1], u2 = hi53(r2) 2^-53 in [0,1);
  *   g = sqrt(-2 ln u1) cos(2 pi u2)                          (Box-Muller);
  *   G[j][t*m + l] = g rounded to FP32 (compute = 0), or that FP32 value rounded
- *   to bfloat16 (compute = 1);
+ *   to bfloat16 (compute = 1) or to FP8 E4M3 (compute = 3);
  * then b and ka/kb exactly as in orc_family_tables.
  * G is [d][m*L] row-major.
  */
@@ -154,7 +171,8 @@ void orc_dense_family(uint64_t seed, int L, int d, int m, double w, int compute,
         double u2 = (double)(r2 >> 11) * 0x1.0p-53;
         double g = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
         float g32 = (float)g;
-        G[(int64_t)j * ldg + (int64_t)t * m + l] = compute == 1 ? orc_round_bf16(g32) : g32;
+        G[(int64_t)j * ldg + (int64_t)t * m + l] =
+            compute == 1 ? orc_round_bf16(g32) : compute == 3 ? (float)orc_round_e4m3((double)g32) : g32;
       }
     }
     for (int l = 0; l < m; ++l) {
@@ -203,7 +221,9 @@ double orc_from_e4m3(uint8_t q) {
   return s ? -v : v;
 }
 
-/* dtype codes: 0 = f32, 1 = bf16, 2 = f16, 3 = fp8 e4m3 (x = scale[row] * q). */
+/* dtype codes: 0 = f32, 1 = bf16, 2 = f16, 3 = fp8 e4m3 (x = scale[row] * q;
+ * the projection of such a row is scale[row] times the projection of its
+ * FP8 values q, one FP64 multiply after the sum -- see orc_hash_dense). */
 static double orc_load(const void *X, int dtype, int64_t idx) {
   switch (dtype) {
   case 0: return orc_from_f32(((const float *)X)[idx]);
@@ -213,12 +233,12 @@ static double orc_load(const void *X, int dtype, int64_t idx) {
   }
 }
 
-/* Row `i` of X widened to FP64 (d entries; ld = row stride in elements). */
+/* Row `i` of X widened to FP64 (d entries; ld = row stride in elements);
+ * FP8 rows are returned unscaled. */
 void orc_load_row(const void *X, int dtype, const float *row_scale, int64_t ld,
                   int64_t i, int d, double *x) {
   for (int j = 0; j < d; ++j) {
     double v = orc_load(X, dtype, i * ld + j);
-    if (dtype == 3 && row_scale) v = (double)row_scale[i] * v;
     x[j] = v;
   }
 }
@@ -368,8 +388,13 @@ int orc_hash_dense(const orc_family *f, const void *X, int dtype,
     orc_load_row(X, dtype, row_scale, ld, i, d, x);
     for (int j = 0; j < d; ++j)
       if (!isfinite(x[j])) status |= 2;
+    const double rs = (dtype == 3 && row_scale) ? (double)row_scale[i] : 1.0;
+    if (!isfinite(rs)) status |= 2;
     for (int t = 0; t < L; ++t) {
       orc_project_table(f, x, t, y);
+      /* a per-row-scaled FP8 row: y = scale * (projection of q), one rounding */
+      if (dtype == 3 && row_scale)
+        for (int l = 0; l < m; ++l) y[l] = rs * y[l];
       for (int l = 0; l < m; ++l) {
         int err = 0;
         c[l] = srp ? orc_srp_bit(y[l]) : orc_e2lsh_code(y[l], scale, f->b[t * m + l], f->w, &err);

@@ -46,6 +46,26 @@ inline float to_bf16(float f) {
   return f;
 }
 
+// Round a finite FP32 value to the nearest FP8 E4M3 value (3 fraction bits,
+// exponent bias 7, subnormal quantum 2^-9, largest finite 448), ties to even,
+// saturating; integer rounding of the FP32 significand, widened back.
+inline float to_e4m3(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t sign = u & 0x80000000u, a = u & 0x7FFFFFFFu;
+  if (a < 0x00800000u) return sign ? -0.f : 0.f;  // zero or an FP32 subnormal: below 2^-10
+  const int e = int(a >> 23) - 127;
+  const int shift = e >= -6 ? 20 : 20 + (-6 - e);  // significand bits below the E4M3 quantum
+  if (shift > 24) return sign ? -0.f : 0.f;
+  const uint32_t mant = (a & 0x7FFFFFu) | 0x800000u;
+  uint32_t keep = mant >> shift;
+  const uint32_t rem = mant & ((1u << shift) - 1u), half = 1u << (shift - 1);
+  if (rem > half || (rem == half && (keep & 1u))) ++keep;
+  double v = std::ldexp(double(keep), e - 23 + shift);
+  if (v > 448.0) v = 448.0;
+  return float(sign ? -v : v);
+}
+
 void draw_offsets_and_keys(Stream &s, const lsh_family_desc &d, int t, HostFamily &hf) {
   const int m = d.m;
   for (int l = 0; l < m; ++l) hf.b[size_t(t) * m + l] = d.w * unit53(s.next());
@@ -79,7 +99,8 @@ void sample_family(const lsh_family_desc &d, HostFamily &hf) {
           const double radius = std::sqrt(-2.0 * std::log(u1));
           const double g = radius * std::cos(two_pi * u2);
           const float g32 = float(g);
-          hf.G[size_t(j) * ldg + size_t(t) * m + l] = d.compute == LSH_BF16 ? to_bf16(g32) : g32;
+          hf.G[size_t(j) * ldg + size_t(t) * m + l] =
+              d.compute == LSH_BF16 ? to_bf16(g32) : d.compute == LSH_FP8_E4M3 ? to_e4m3(g32) : g32;
         }
       draw_offsets_and_keys(s, d, t, hf);
     }

@@ -82,6 +82,7 @@ struct lsh_family_s {
   float *d_Gt = nullptr;          // [m*L][d] transposed copy (FP64 recheck reads columns)
   float *d_gnorm = nullptr;       // [m*L] column norms, rounded up
   uint16_t *d_Gt16 = nullptr;     // [m*L][d] bf16 bits (families with BF16 G)
+  uint8_t *d_Gt8 = nullptr;       // [m*L][d] E4M3 codes (families with FP8 G)
   float *d_gnc = nullptr;         // [m*L][4] column norms per K chunk of the tensor-core path;
                                   // slots 2, 3: the column's least exponent and its range (int bits)
   int32_t *d_Gint = nullptr;      // [m*L][d] column j of G as integers on its own 2^e grid (exact recheck)
@@ -117,6 +118,7 @@ struct SketchLaunch {
   const void *X;
   int32_t dtype;
   int64_t n, ld;
+  const float *row_scale;  // FP8 rows: [n] scales (x = scale * q)
   int32_t d;
   // family
   int32_t kind, m, L, N;
@@ -173,9 +175,9 @@ cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float
 // Dense E2LSH / SRP on the tensor cores (TMA + tcgen05, BF16 x BF16 -> FP32),
 // for BF16 rows and a family whose G is stored in BF16.  xnc_scratch: [n][4] floats.
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X);
-int tc_chunk_ktiles(int d);
+int tc_chunk_ktiles(int d, bool fp8);
 size_t tc_dense_scratch_bytes(int64_t n, int64_t ML);
-cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
+cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float *Gt, const float *gnc,
                             const int32_t *Gint, void *scratch, cudaStream_t stream);
 
 // Query path: probe + dedup + exact top-k rerank, G CTAs per query

@@ -39,8 +39,8 @@ lsh_status validate_desc(const lsh_family_desc &d) {
   if (d.L < 1) return fail(LSH_EINVAL, "L must be >= 1");
   if (!(d.w > 0.0) || !std::isfinite(d.w)) return fail(LSH_EINVAL, "w must be finite and > 0");
   if (kind_is_dense(d.kind)) {
-    if (d.compute != LSH_F32 && d.compute != LSH_BF16)
-      return fail(LSH_EUNSUPPORTED, "dense families store G in FP32 or BF16");
+    if (d.compute != LSH_F32 && d.compute != LSH_BF16 && d.compute != LSH_FP8_E4M3)
+      return fail(LSH_EUNSUPPORTED, "dense families store G in FP32, BF16 or FP8 E4M3");
     if (int64_t(d.d) * d.m * d.L > (int64_t(1) << 31)) return fail(LSH_EINVAL, "G too large");
     return LSH_OK;
   }
@@ -83,6 +83,7 @@ void free_family(lsh_family_s *f) {
   cudaFree(f->d_Gt16);
   cudaFree(f->d_gnc);
   cudaFree(f->d_Gint);
+  cudaFree(f->d_Gt8);
   cudaFree(f->d_status);
   cudaFree(f->d_colmajor);
   cudaFree(f->d_mlist);
@@ -120,9 +121,12 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   const lsh_family_desc &d = f->host.desc;
   if (X->n == 0) return LSH_OK;
   if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
-  if (X->dtype == LSH_FP8_E4M3 && !X->rowptr) return fail(LSH_EUNSUPPORTED, "FP8 input is for the dense kinds");
+  if (X->dtype == LSH_FP8_E4M3 && !(f->d_Gt8 && tc_dense_supported(d, X)))
+    return fail(LSH_EUNSUPPORTED, "FP8 rows are hashed by dense families with an FP8 G on the tensor cores "
+                                  "(d and the row stride multiples of 16, m in 8..64 dividing 64, m*L a multiple of 128)");
   SketchLaunch p{};
   p.X = X->values;
+  p.row_scale = X->row_scale;
   p.dtype = X->dtype;
   p.n = X->n;
   p.ld = X->ld;
@@ -154,10 +158,11 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.proj = proj;
   p.counters = counters;
   p.status = f->d_status;
-  if (kind_is_dense(d.kind) && f->d_Gt16 && tc_dense_supported(d, X)) {
+  if (kind_is_dense(d.kind) && (f->d_Gt16 || f->d_Gt8) && tc_dense_supported(d, X)) {
     void *scratch = nullptr;
     LSH_CUDA_TRY(cudaMallocAsync(&scratch, tc_dense_scratch_bytes(X->n, int64_t(d.m) * d.L), stream));
-    const cudaError_t e = launch_tc_dense(p, f->d_Gt16, f->d_Gt, f->d_gnc, f->d_Gint, scratch, stream);
+    const void *gtc = X->dtype == LSH_FP8_E4M3 ? static_cast<const void *>(f->d_Gt8) : f->d_Gt16;
+    const cudaError_t e = launch_tc_dense(p, gtc, f->d_Gt, f->d_gnc, f->d_Gint, scratch, stream);
     cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core dense hash");
     count_launches(3);
@@ -306,15 +311,52 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
     }
     if (e == cudaSuccess) e = upload(&f->d_Gt, gt.data(), gt.size());
     if (e == cudaSuccess) e = upload(&f->d_gnorm, gn.data(), gn.size());
-    if (e == cudaSuccess && d.compute == LSH_BF16) {
-      // bf16 copy of G^T for the tensor cores, and its column norms per K chunk
-      std::vector<uint16_t> g16(gt.size());
+    if (e == cudaSuccess && (d.compute == LSH_BF16 || d.compute == LSH_FP8_E4M3)) {
+      // the compact copy of G^T for the tensor cores (bf16 bits or E4M3 codes),
+      // its column norms per K chunk, and each column as integers on the grid
+      // of its least exponent (a value is M 2^E, M < 256 resp. M < 16)
+      const bool fp8 = d.compute == LSH_FP8_E4M3;
+      auto parts = [fp8](float v, int32_t &M, int &E) -> bool {  // false for zero
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        const uint32_t a = u & 0x7FFFFFFFu;
+        if (a == 0) return false;
+        const int ef = int(a >> 23) - 127;
+        if (!fp8) {  // bf16: 7 stored fraction bits
+          const uint32_t ex = a >> 23, fr = (a >> 16) & 0x7F;
+          M = int32_t(ex ? (fr | 0x80) : fr);
+          E = ex ? int(ex) - 134 : -133;
+        } else if (ef >= -6) {  // normal E4M3: 3 fraction bits
+          M = int32_t(8 + ((a >> 20) & 7));
+          E = ef - 3;
+        } else {  // subnormal E4M3: f 2^-9
+          M = int32_t(std::ldexp(double(v < 0 ? -v : v), 9));
+          E = -9;
+        }
+        if (u >> 31) M = -M;
+        return true;
+      };
+      std::vector<uint16_t> g16;
+      std::vector<uint8_t> g8;
+      if (fp8) g8.resize(gt.size());
+      else g16.resize(gt.size());
       for (size_t i = 0; i < gt.size(); ++i) {
         uint32_t u;
         std::memcpy(&u, &gt[i], 4);
-        g16[i] = uint16_t(u >> 16);  // exact: the entries are bf16 values
+        if (!fp8) {
+          g16[i] = uint16_t(u >> 16);  // exact: the entries are bf16 values
+        } else {
+          int32_t M = 0;
+          int E = 0;
+          uint8_t code = 0;
+          if (parts(gt[i], M, E)) {
+            const uint32_t am = uint32_t(M < 0 ? -M : M);
+            code = E == -9 && am < 8 ? uint8_t(am) : uint8_t(((E + 10) << 3) | (am - 8));
+          }
+          g8[i] = uint8_t(code | ((u >> 24) & 0x80));
+        }
       }
-      const int clen = tc_chunk_ktiles(d.d) * 64;
+      const int clen = tc_chunk_ktiles(d.d, fp8) * (fp8 ? 128 : 64);
       std::vector<float> gnc(ml * 4, 0.f);
       std::vector<int32_t> gint(gt.size(), 0);
       for (size_t c = 0; c < ml; ++c) {
@@ -323,13 +365,12 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
           for (int j = k * clen; j < std::min(d.d, (k + 1) * clen); ++j) s2 += double(gt[c * d.d + j]) * gt[c * d.d + j];
           gnc[c * 4 + k] = float(std::sqrt(s2) * (1.0 + 1e-6));
         }
-        // bf16 g = M 2^E (M < 256 an integer): the column on the grid of its least exponent
         int emin = 0, emax = 0;
         bool any = false;
         for (int j = 0; j < d.d; ++j) {
-          const uint32_t h = g16[c * d.d + j], ex = (h >> 7) & 0xFF, fr = h & 0x7F;
-          if (ex == 0 && fr == 0) continue;
-          const int E = ex ? int(ex) - 134 : -133;
+          int32_t M;
+          int E;
+          if (!parts(gt[c * d.d + j], M, E)) continue;
           emin = any ? std::min(emin, E) : E;
           emax = any ? std::max(emax, E) : E;
           any = true;
@@ -337,18 +378,19 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
         const int range = emax - emin;
         if (range <= 23)
           for (int j = 0; j < d.d; ++j) {
-            const uint32_t h = g16[c * d.d + j], ex = (h >> 7) & 0xFF, fr = h & 0x7F;
-            if (ex == 0 && fr == 0) continue;
-            const int32_t M = int32_t(ex ? (fr | 0x80) : fr) << ((ex ? int(ex) - 134 : -133) - emin);
-            gint[c * d.d + j] = (h >> 15) ? -M : M;
+            int32_t M;
+            int E;
+            if (parts(gt[c * d.d + j], M, E)) gint[c * d.d + j] = M * (int32_t(1) << (E - emin));
           }
         int32_t slots[2] = {emin, range};
         std::memcpy(&gnc[c * 4 + 2], slots, sizeof(slots));
       }
-      e = upload(&f->d_Gt16, g16.data(), g16.size());
+      if (fp8) e = upload(&f->d_Gt8, g8.data(), g8.size());
+      else e = upload(&f->d_Gt16, g16.data(), g16.size());
       if (e == cudaSuccess) e = upload(&f->d_gnc, gnc.data(), gnc.size());
       if (e == cudaSuccess) e = upload(&f->d_Gint, gint.data(), gint.size());
     }
+
   }
   if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {
     // column-major copy of the count-sketch tables for the CSR kernel

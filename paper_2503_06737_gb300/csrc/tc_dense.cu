@@ -40,20 +40,24 @@
 namespace lsh {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, KMAX = 8, SB = 5, NCH = 2;
+constexpr int BM = 128, BN = 128, KMAX = 8, SB = 5, NCH = 2;
+constexpr int BKB = 128;  // bytes of K per tile row: 64 BF16 or 128 E4M3 elements (one 128-byte swizzle row)
 constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps;
 constexpr int CONST_Q = 5;
 constexpr int BW = 8;  // epilogue block: columns read from TMEM at a time  // per-column constants staged per epilogue warp: gn0, gn1, b, ka, kb
-constexpr int XNC_LD = 4, GNC_LD = 4;  // row / column records: NCH chunk norms, then exponent base and range
+constexpr int XNC_LD = 8, GNC_LD = 4;  // row / column records: NCH chunk norms, exponent base and range
+                                       // (rows: then the FP8 row scale)
 static_assert(NCH <= 2, "the chunk norms share a four-word record with the exponent range");
-constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;
+constexpr int TILE_A = BM * BKB, TILE_B = BN * BKB;
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr float kU = 5.9604644775390625e-08f;
 
 struct TcArgs {
   int64_t n, mtiles, ML;
   int32_t d, m, L, srp, ktiles, ktpc, nch;
-  const unsigned short *X;   // bf16 rows
+  const void *X;             // bf16 rows, or E4M3 codes (fp8) with row_scale
+  const float *row_scale;
+  int32_t fp8;
   int64_t ld;
   const float *Gt;           // [mL][d] FP32 copy (sequential recheck fallback)
   const int32_t *Gint;       // [mL][d] columns of G as integers on their own grids (exact recheck)
@@ -130,11 +134,18 @@ __device__ __forceinline__ void tma_2d_elect(void *dst, const CUtensorMap *map, 
       " @e cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n}\n"
       ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(x), "r"(y), "r"(bytes) : "memory");
 }
+template <bool FP8>
 __device__ __forceinline__ void umma_elect(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  if (FP8)
+    asm volatile(
+        "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit_elect(uint64_t *bar) {
   asm volatile(
@@ -152,6 +163,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -160,27 +175,45 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// FP64 value of one projection, sum_j x_j G[j][c] in ascending j with one
-// IEEE rounding per operation.  Rows are 16-byte aligned and d % 8 == 0 on
-// this path, so eight terms are loaded at once before their sequential adds.
+// Element k of a 16-byte chunk: BF16 (eight) or E4M3 (sixteen) as a value
+// M 2^E with M an integer (|M| < 256 resp. < 16); the sign separately.
+__device__ __forceinline__ void elem_parts(const uint32_t (&w)[4], int k, bool fp8, int &M, int &E, uint32_t &neg) {
+  if (!fp8) {
+    const uint32_t h = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+    const int e = (h >> 7) & 0xFF;
+    M = int(h & 0x7F) | (min(e, 1) << 7);
+    E = max(e, 1) - 134;
+    neg = h >> 15;
+  } else {
+    const uint32_t h = (w[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+    const int e = (h >> 3) & 15;
+    M = int(h & 7) | (min(e, 1) << 3);
+    E = max(e, 1) - 10;
+    neg = h >> 7;
+  }
+}
+
+// FP64 value of one projection as the oracle computes it: sum_j x_j G[j][c]
+// in ascending j, one IEEE rounding per operation; for an FP8 row the sum is
+// over its E4M3 values and the row scale multiplies it once at the end.
+// Rows are 16-byte aligned and d a multiple of the 16-byte chunk on this path.
 __device__ __noinline__ double tc_fp64(const TcArgs &a, int64_t row, int64_t col) {
   const float *g = a.Gt + col * a.d;
-  const unsigned short *x = a.X + row * a.ld;
+  const int per = a.fp8 ? 16 : 8;
+  const uint4 *xr = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.X) + row * a.ld * (a.fp8 ? 1 : 2));
   double y = 0.0;
-#pragma unroll 2
-  for (int j = 0; j < a.d; j += 8) {
-    const uint4 xv = *reinterpret_cast<const uint4 *>(x + j);
-    const float4 g0 = *reinterpret_cast<const float4 *>(g + j);
-    const float4 g1 = *reinterpret_cast<const float4 *>(g + j + 4);
-    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-    const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t h = (k & 1) ? (xw[k >> 1] >> 16) : (xw[k >> 1] & 0xFFFFu);
-      y = __dadd_rn(y, __dmul_rn(double(__uint_as_float(h << 16)), double(gv[k])));
+  for (int c = 0; c < a.d / per; ++c) {
+    const uint4 xv = xr[c];
+    const uint32_t w[4] = {xv.x, xv.y, xv.z, xv.w};
+    for (int k = 0; k < per; ++k) {
+      int M, E;
+      uint32_t neg;
+      elem_parts(w, k, a.fp8 != 0, M, E, neg);
+      const double x = ldexp(double(neg ? -M : M), E);  // exact
+      y = __dadd_rn(y, __dmul_rn(x, double(g[c * per + k])));
     }
   }
-  return y;
+  return a.fp8 ? __dmul_rn(double(a.row_scale[row]), y) : y;
 }
 
 // The FP64 value of sum_j x_j G[j][c] (ascending j, one rounding per
@@ -204,28 +237,32 @@ __device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, in
   const int4 xi = __ldg(reinterpret_cast<const int4 *>(a.xnc + row * XNC_LD));
   const int4 gi = __ldg(reinterpret_cast<const int4 *>(a.gnc + col * GNC_LD));
   const int ex0 = xi.z, rx = xi.w, eg0 = gi.z, rg = gi.w;
-  const uint4 *xr = reinterpret_cast<const uint4 *>(a.X + row * a.ld);
+  const bool fp8 = a.fp8 != 0;
+  const int per = fp8 ? 16 : 8;  // elements per 16-byte chunk
+  const uint4 *xr = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.X) + row * a.ld * (fp8 ? 1 : 2));
   const int4 *gr = reinterpret_cast<const int4 *>(a.Gint + col * a.d);
   // two's complement sum (wraps harmlessly when the magnitude test fails);
   // the magnitude saturates at 2^53 so that neither a lane nor the reduction overflows
   unsigned long long sum = 0, mag = 0;
   constexpr unsigned long long kCap = 1ull << 53;
-  const int nch = a.d >> 3;  // chunks of eight coordinates
-#pragma unroll 4
+  const int nch = a.d / per;
+#pragma unroll 2
   for (int c = gl; c < nch; c += G) {
     const uint4 xv = __ldg(xr + c);
-    const int4 g0 = __ldg(gr + 2 * c), g1 = __ldg(gr + 2 * c + 1);
-    const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-    const int gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    const uint32_t w[4] = {xv.x, xv.y, xv.z, xv.w};
+    for (int h = 0; h < per; h += 8) {
+      const int4 g0 = __ldg(gr + (c * per + h) / 4), g1 = __ldg(gr + (c * per + h) / 4 + 1);
+      const int gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t h = (k & 1) ? (xw[k >> 1] >> 16) : (xw[k >> 1] & 0xFFFFu);
-      const int ex = (h >> 7) & 0xFF;
-      const int M = int(h & 0x7F) | (min(ex, 1) << 7);  // implicit bit unless subnormal
-      const int X = M << max(max(ex, 1) - 134 - ex0, 0);  // zero stays zero
-      const long long P = (long long)X * gv[k];
-      sum += (unsigned long long)((h >> 15) ? -P : P);
-      mag += (unsigned long long)(P < 0 ? -P : P);
+      for (int k = 0; k < 8; ++k) {
+        int M, E;
+        uint32_t neg;
+        elem_parts(w, h + k, fp8, M, E, neg);
+        const int X = M << max(E - ex0, 0);  // zero stays zero
+        const long long P = (long long)X * gv[k];
+        sum += (unsigned long long)(neg ? -P : P);
+        mag += (unsigned long long)(P < 0 ? -P : P);
+      }
     }
     mag = min(mag, kCap);
   }
@@ -236,7 +273,16 @@ __device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, in
   }
   S = (long long)sum;
   e = ex0 + eg0;
-  return rx <= 23 && rg <= 23 && rx + rg <= 37 && mag < kCap;
+  // every product below 2^53: (M bits) + Rx + (M bits) + Rg <= 53
+  const int mbits = fp8 ? 4 : 8;
+  return rx <= 23 && rg <= 23 && 2 * mbits + rx + rg <= 53 && mag < kCap;
+}
+
+// The oracle's FP64 projection from an exact sum S 2^e: exact, then (FP8 rows)
+// one multiply by the row scale.
+__device__ __forceinline__ double y_exact(const TcArgs &a, int64_t row, long long S, int e) {
+  const double y = ldexp(double(S), e);
+  return a.fp8 ? __dmul_rn(double(a.row_scale[row]), y) : y;
 }
 
 // The oracle's code from the FP64 projection: SRP the sign, E2LSH
@@ -266,7 +312,7 @@ __device__ __forceinline__ void recheck_block(const TcArgs &a, int64_t row, int 
       int e;
       const bool ok = exact_sum_group<32>(a, lrow, col, lane, S, e);
       if (lane == leader) {
-        const int c64 = (SRP && ok) ? int(S > 0) : code_from_fp64(a, ok ? ldexp(double(S), e) : tc_fp64(a, lrow, col), col, novf);
+        const int c64 = code_from_fp64(a, ok ? y_exact(a, lrow, S, e) : tc_fp64(a, lrow, col), col, novf);
         ++nflag;
 #pragma unroll
         for (int k = 0; k < W; ++k)
@@ -285,7 +331,7 @@ __device__ __forceinline__ void recheck_block(const TcArgs &a, int64_t row, int 
 // i % 2 while the epilogue warps drain the other one.  Epilogue warp e reads
 // TMEM lanes 32 (e % 4) .. +31 (the rows it may access) and the 32-column
 // slice e / 4; M (the bins per table) is a compile-time power of two.
-template <bool SRP, int M>
+template <bool SRP, int M, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                const __grid_constant__ CUtensorMap mapB,
                                                                const TcArgs a) {
@@ -300,6 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   __shared__ volatile int aborted;  // set on a timed-out wait: later waits are skipped
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int ntn = int(a.ML / BN);
+  constexpr int kBKE = FP8 ? BKB : BKB / 2;  // K elements per tile (TMA coordinates are in elements)
 
   if (threadIdx.x == 0) {
     aborted = 0;
@@ -344,13 +391,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
               ok = false;
               break;
             }
-            tma_2d_elect(sA + kt * TILE_A, &mapA, &afull[kt], TILE_A, kt * BK, m0);
+            tma_2d_elect(sA + kt * TILE_A, &mapA, &afull[kt], TILE_A, kt * kBKE, m0);
           }
           if (__any_sync(0xffffffffu, aborted != 0) || (it >= SB && !mbar_wait_warp(&bempty[s], sph ^ 1))) {
             ok = false;
             break;
           }
-          tma_2d_elect(sB + s * TILE_B, &mapB, &bfull[s], TILE_B, kt * BK, n0);
+          tma_2d_elect(sB + s * TILE_B, &mapB, &bfull[s], TILE_B, kt * kBKE, n0);
           if (++s == SB) {
             s = 0;
             sph ^= 1;
@@ -371,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
     // MMA issue: the whole warp walks the loop, one elected lane issues.
     // Descriptors are precomputed and advanced by adding to their address
     // field (shared addresses < 2^18 never carry out of it).
-    const uint32_t idesc = idesc_bf16(BM, BN);
+    const uint32_t idesc = FP8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
     const uint64_t adesc0 = sdesc(su32(sA)), bdesc0 = sdesc(su32(sB));
     uint32_t i = 0, mi = 0, s = 0, sph = 0;
     bool ok = true;
@@ -391,9 +438,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
             break;
           }
           const uint64_t ad = adesc0 + uint64_t(kt * (TILE_A >> 4)), bd = bdesc0 + uint64_t(s * (TILE_B >> 4));
+          // four MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3 elements)
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            umma_elect(dt, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc, (kc == 0 && k == 0) ? 0u : 1u);
+          for (int k = 0; k < 4; ++k)
+            umma_elect<FP8>(dt, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc, (kc == 0 && k == 0) ? 0u : 1u);
           commit_elect(&bempty[s]);
           if (j == ntn - 1) commit_elect(&aempty[kt]);
           if (++s == SB) {
@@ -424,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
     // plus that of adding them (kE (|c0| + |c1|) <= kE 1.01 sum_c ||x_c|| ||g_c||).
     // E2LSH folds 1.0001 / w into g_c: the bound on t is then xs0 g0 + xs1 g1
     // + 10.2 u |t| + 15.3 u.
-    const float steps = float(a.ktpc * (BK / 16));
+    const float steps = float(a.ktpc * 4);  // MMA steps per K chunk
     const float kE = 2.f * kU * 1.02f;
     const float invw = a.invw, gscale = SRP ? 1.f : a.invw * 1.0001f;
     // per-column constants of this warp's slice: [g0 x8][g1 x8][b x8][ka x8][kb x8] as float4
@@ -433,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
     const int64_t Tend = a.mtiles * ntn;
     auto next_tile = [&](int64_t T) { return T + (((T + 1) % ntn == 0) ? int64_t(gridDim.x - 1) * ntn + 1 : 1); };
     // the next tile's constants are loaded while this one is processed
-    float pg0 = 0.f, pg1 = 0.f, pb = 0.f, pka = 0.f, pkb = 0.f, px0 = 0.f, px1 = 0.f;
+    float pg0 = 0.f, pg1 = 0.f, pb = 0.f, pka = 0.f, pkb = 0.f, px0 = 0.f, px1 = 0.f, psc = 1.f;
     auto prefetch = [&](int64_t T) {
       if (T >= Tend) return;
       const int col = int((rot + T % ntn) % ntn) * BN + slice * 32 + lane;
@@ -447,10 +495,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
         pkb = __uint_as_float(__ldg(a.kb + col));
       }
       px0 = px1 = 0.f;
+      psc = 1.f;
       if (prow < a.n) {
         const float2 xv = __ldg(reinterpret_cast<const float2 *>(a.xnc + prow * XNC_LD));
         px0 = xv.x;
         px1 = xv.y;
+        if (FP8) psc = __ldg(a.xnc + prow * XNC_LD + 4);  // the row scale (NaN-checked by the pre-pass)
       }
     };
     prefetch(int64_t(blockIdx.x) * ntn);
@@ -473,7 +523,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
       }
       const bool valid = row < a.n;
       const bool bad = valid && !(isfinite(px0) && isfinite(px1));
-      const float xs[NCH] = {kE * (steps + 1.01f) * px0, kE * (steps + 1.01f) * px1};
+      // FP8 rows: the accumulator holds q.G, the projection is scale * that
+      const float rsc = psc, ars = fabsf(psc);
+      const float xs[NCH] = {kE * (steps + 1.01f) * px0 * ars, kE * (steps + 1.01f) * px1 * ars};
       if (bad && n0 == 0) ++nbad;
       prefetch(next_tile(T));
       // on a timeout the warp goes on without waiting (the status reports the
@@ -520,16 +572,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int j = g4 * 4 + u;
-            const float y = ch[0][j] + ch[1][j];
+            // FP8: the scale multiply adds one rounding, u |y| (<= u (|t| + 1) w): wider constants
+            const float y = FP8 ? __fmul_rn(rsc, ch[0][j] + ch[1][j]) : ch[0][j] + ch[1][j];
             bool flag;
             if (SRP) {
               const float E = fmaf(xs[0], gg0[u], xs[1] * gg1[u]);
               code[j] = y > 0.f ? 1 : 0;
-              flag = !(fabsf(y) > E);
+              flag = !((FP8 ? fabsf(y) * (1.f - 2.f * kU) : fabsf(y)) > E);
             } else {
               const float tf = __fmul_rn(y + bv[u], invw);
               const float dist = fabsf(tf - rintf(tf));  // exact
-              const float Mb = fmaf(xs[0], gg0[u], fmaf(xs[1], gg1[u], fmaf(10.2f * kU, fabsf(tf), 15.3f * kU)));
+              const float Mb = fmaf(xs[0], gg0[u], fmaf(xs[1], gg1[u], fmaf((FP8 ? 11.3f : 10.2f) * kU, fabsf(tf),
+                                                                             (FP8 ? 16.4f : 15.3f) * kU)));
               code[j] = __float2int_rd(tf);
               flag = !(dist > Mb && fabsf(tf) < 4194304.f);
             }
@@ -540,8 +594,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
 #pragma unroll
           for (int j = 0; j < BW; j += 4)
             *reinterpret_cast<float4 *>(a.proj + row * a.ML + col0 + j) =
-                make_float4(ch[0][j] + ch[1][j], ch[0][j + 1] + ch[1][j + 1], ch[0][j + 2] + ch[1][j + 2],
-                            ch[0][j + 3] + ch[1][j + 3]);
+                FP8 ? make_float4(__fmul_rn(rsc, ch[0][j] + ch[1][j]), __fmul_rn(rsc, ch[0][j + 1] + ch[1][j + 1]),
+                                  __fmul_rn(rsc, ch[0][j + 2] + ch[1][j + 2]), __fmul_rn(rsc, ch[0][j + 3] + ch[1][j + 3]))
+                    : make_float4(ch[0][j] + ch[1][j], ch[0][j + 1] + ch[1][j + 1], ch[0][j + 2] + ch[1][j + 2],
+                                  ch[0][j + 3] + ch[1][j + 3]);
         if (!valid || bad) fmask = 0;
         // 2. the rare slow path: queue the flagged entries for the recheck
         //    kernel; entries beyond the queue's capacity are rechecked here
@@ -692,8 +748,7 @@ __global__ void __launch_bounds__(256) tc_recheck_kernel(const TcArgs a) {
     }
     if (mine) {
       const int64_t row = r.x, col = r.y;
-      const int c64 = (a.srp && okm) ? int(Sm > 0)
-                                     : code_from_fp64(a, okm ? ldexp(double(Sm), em) : tc_fp64(a, row, col), col, novf);
+      const int c64 = code_from_fp64(a, okm ? y_exact(a, row, Sm, em) : tc_fp64(a, row, col), col, novf);
       ++nflag;
       if (c64 != r.z) {
         ++nchanged;
@@ -730,11 +785,13 @@ __global__ void __launch_bounds__(256) tc_recheck_kernel(const TcArgs a) {
 }
 
 // Row records: chunk norms ||x_chunk|| widened to an upper bound (NaN when
-// the row is not finite), then the least exponent and the exponent range of
-// the nonzero coordinates (x = M 2^E, M < 256).  Warp per row, 16-byte loads
-// (d and the row stride are multiples of eight on this path).
-__global__ void __launch_bounds__(256) row_chunk_norms(const unsigned short *X, int64_t n, int d, int64_t ld,
-                                                       int chunk_len, float *out) {
+// the row -- or its FP8 scale -- is not finite), then the least exponent and
+// the exponent range of the nonzero coordinates (x = M 2^E, M an integer),
+// then the FP8 row scale.  FP8 rows are measured unscaled (the accumulator
+// holds q.G).  Warp per row, 16-byte loads (d and the row stride are
+// multiples of the 16-byte chunk on this path).
+__global__ void __launch_bounds__(256) row_chunk_norms(const void *X, int fp8, const float *row_scale, int64_t n,
+                                                       int d, int64_t ld, int chunk_len, float *out) {
   const int64_t row = int64_t(blockIdx.x) * 8 + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= n) return;
@@ -743,21 +800,28 @@ __global__ void __launch_bounds__(256) row_chunk_norms(const unsigned short *X, 
   for (int cc = 0; cc < NCH; ++cc) s[cc] = 0.f;
   bool fin = true;
   int emin = 1 << 20, emax = -(1 << 20);
-  const uint4 *xr = reinterpret_cast<const uint4 *>(X + row * ld);
-  for (int c = lane; c < (d >> 3); c += 32) {
+  const int per = fp8 ? 16 : 8;
+  const uint4 *xr = reinterpret_cast<const uint4 *>(static_cast<const char *>(X) + row * ld * (fp8 ? 1 : 2));
+  for (int c = lane; c < d / per; c += 32) {
     const uint4 v4 = xr[c];
     const uint32_t w[4] = {v4.x, v4.y, v4.z, v4.w};
-    const int ch = min((c * 8) / chunk_len, NCH - 1);
+    const int ch = min((c * per) / chunk_len, NCH - 1);
     float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t h = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
-      const float v = __uint_as_float(h << 16);
+    for (int k = 0; k < per; ++k) {
+      int M, E;
+      uint32_t neg;
+      elem_parts(w, k, fp8 != 0, M, E, neg);
+      float v;
+      if (!fp8) {
+        const uint32_t h = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+        v = __uint_as_float(h << 16);
+      } else {
+        const uint32_t h = (w[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        v = ((h & 0x7F) == 0x7F) ? __int_as_float(0x7fc00000) : ldexpf(float(M), E);  // E4M3 NaN code
+      }
       fin = fin && isfinite(v);
       acc = fmaf(v, v, acc);
-      const int e = (h >> 7) & 0xFF;
-      if (h & 0x7FFF) {
-        const int E = max(e, 1) - 134;
+      if (M) {
         emin = min(emin, E);
         emax = max(emax, E);
       }
@@ -773,7 +837,8 @@ __global__ void __launch_bounds__(256) row_chunk_norms(const unsigned short *X, 
     emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
     emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   }
-  const bool allfin = __all_sync(0xffffffffu, fin);
+  const float sc = fp8 ? row_scale[row] : 1.f;
+  const bool allfin = __all_sync(0xffffffffu, fin) && isfinite(sc);
   if (emax < emin) emin = emax = 0;  // an all-zero row
   if (lane < NCH) {
     float v = 0.f;
@@ -787,6 +852,8 @@ __global__ void __launch_bounds__(256) row_chunk_norms(const unsigned short *X, 
     out[row * XNC_LD + 2] = __int_as_float(emin);
   } else if (lane == 3) {
     out[row * XNC_LD + 3] = __int_as_float(emax - emin);
+  } else if (lane == 4) {
+    out[row * XNC_LD + 4] = sc;
   }
 }
 
@@ -808,22 +875,26 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap *map, const void *base, int64_t rows, int K, int64_t row_stride_elems) {
+// Tile map over a row-major [rows][K] matrix of 1- or 2-byte elements: boxes
+// of 128 rows x 128 bytes (64 BF16 or 128 E4M3), 128-byte swizzle.
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int K, int64_t row_stride_elems, bool fp8) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
+  const int es = fp8 ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * 2};
-  cuuint32_t box[2] = {BK, 128};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * es};
+  cuuint32_t box[2] = {(cuuint32_t)(BKB / es), 128};
   cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
+             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-int tc_chunk_ktiles(int d) {
-  const int ktiles = (d + BK - 1) / BK;
+int tc_chunk_ktiles(int d, bool fp8) {
+  const int bk = fp8 ? BKB : BKB / 2;  // elements per K tile
+  const int ktiles = (d + bk - 1) / bk;
   return (ktiles + NCH - 1) / NCH;
 }
 
@@ -841,31 +912,40 @@ size_t tc_dense_scratch_bytes(int64_t n, int64_t ML) {
 
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X) {
   const int64_t ML = int64_t(fd.m) * fd.L;
-  if (!kind_is_dense(fd.kind) || fd.compute != LSH_BF16 || !X || X->rowptr || X->dtype != LSH_BF16) return false;
-  if (fd.d % 8 != 0 || X->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(X->values) & 15) != 0) return false;
+  if (!kind_is_dense(fd.kind) || !X || X->rowptr) return false;
+  const bool fp8 = fd.compute == LSH_FP8_E4M3;
+  // the row type is the family's operand type (the MMA takes one type for both)
+  if (!((fd.compute == LSH_BF16 && X->dtype == LSH_BF16) || (fp8 && X->dtype == LSH_FP8_E4M3 && X->row_scale)))
+    return false;
+  const int per = fp8 ? 16 : 8;  // elements per 16 bytes (TMA rows and strides)
+  if (fd.d % per != 0 || X->ld % per != 0 || (reinterpret_cast<uintptr_t>(X->values) & 15) != 0) return false;
   if (ML % BN != 0 || 64 % fd.m != 0) return false;  // a 32-column slice or a pair of them holds whole tables
-  if (fd.d > KMAX * BK) return false;                 // the row tile stays resident in shared memory
+  if (fp8 && fd.m < 8) return false;
+  if (fd.d > KMAX * (fp8 ? BKB : BKB / 2)) return false;  // the row tile stays resident in shared memory
   if (X->n > (int64_t(1) << 31) - BM || (X->n + BM - 1) / BM > 2147483647) return false;
   return encode_fn() != nullptr;
 }
 
-cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, const float *Gt, const float *gnc,
+cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float *Gt, const float *gnc,
                             const int32_t *Gint, void *scratch, cudaStream_t stream) {
   if (p.n <= 0) return cudaSuccess;
-  const int ktiles = (p.d + BK - 1) / BK;
-  const int ktpc = tc_chunk_ktiles(p.d);
+  const bool fp8 = p.dtype == LSH_FP8_E4M3;
+  const int bk = fp8 ? BKB : BKB / 2;
+  const int ktiles = (p.d + bk - 1) / bk;
+  const int ktpc = tc_chunk_ktiles(p.d, fp8);
   const int64_t ML = int64_t(p.m) * p.L;
   float *xnc_scratch = static_cast<float *>(scratch);
   uint32_t *qcount = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + tc_align16(p.n * XNC_LD * 4));
   int4 *queue = reinterpret_cast<int4 *>(qcount + 4);
   cudaError_t e = cudaMemsetAsync(qcount, 0, 16, stream);
   if (e != cudaSuccess) return e;
-  row_chunk_norms<<<(unsigned)((p.n + 7) / 8), 256, 0, stream>>>(static_cast<const unsigned short *>(p.X), p.n, p.d,
-                                                                   p.ld, ktpc * BK, xnc_scratch);
+  row_chunk_norms<<<(unsigned)((p.n + 7) / 8), 256, 0, stream>>>(p.X, fp8 ? 1 : 0, p.row_scale, p.n, p.d, p.ld,
+                                                                   ktpc * bk, xnc_scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
-  if (!make_map(&mA, p.X, p.n, p.d, p.ld) || !make_map(&mB, Gt16, ML, p.d, p.d)) return cudaErrorInvalidValue;
+  if (!make_map(&mA, p.X, p.n, p.d, p.ld, fp8) || !make_map(&mB, Gtc, ML, p.d, p.d, fp8))
+    return cudaErrorInvalidValue;
   TcArgs a{};
   a.n = p.n;
   a.mtiles = (p.n + BM - 1) / BM;
@@ -877,7 +957,9 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, c
   a.ktiles = ktiles;
   a.ktpc = ktpc;
   a.nch = (ktiles + ktpc - 1) / ktpc;
-  a.X = static_cast<const unsigned short *>(p.X);
+  a.X = p.X;
+  a.row_scale = p.row_scale;
+  a.fp8 = fp8 ? 1 : 0;
   a.ld = p.ld;
   a.Gt = Gt;
   a.Gint = Gint;
@@ -901,13 +983,24 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const unsigned short *Gt16, c
   a.qcap = uint32_t(tc_queue_cap(p.n, ML));
   const int smem = KMAX * TILE_A + SB * TILE_B + 1024 + kEpiWarps * CONST_Q * 8 * 16;
   void (*kern)(const CUtensorMap, const CUtensorMap, const TcArgs) = nullptr;
-  switch (p.m * 2 + a.srp) {
-#define LSH_TC_CASE(M)                              \
-  case 2 * M: kern = tc_dense_kernel<false, M>; break; \
-  case 2 * M + 1: kern = tc_dense_kernel<true, M>; break;
-    LSH_TC_CASE(1) LSH_TC_CASE(2) LSH_TC_CASE(4) LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
+  if (!fp8) {
+    switch (p.m * 2 + a.srp) {
+#define LSH_TC_CASE(M)                                        \
+  case 2 * M: kern = tc_dense_kernel<false, M, false>; break; \
+  case 2 * M + 1: kern = tc_dense_kernel<true, M, false>; break;
+      LSH_TC_CASE(1) LSH_TC_CASE(2) LSH_TC_CASE(4) LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
 #undef LSH_TC_CASE
-    default: return cudaErrorInvalidValue;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (p.m * 2 + a.srp) {
+#define LSH_TC_CASE(M)                                       \
+  case 2 * M: kern = tc_dense_kernel<false, M, true>; break; \
+  case 2 * M + 1: kern = tc_dense_kernel<true, M, true>; break;
+      LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
+#undef LSH_TC_CASE
+      default: return cudaErrorInvalidValue;
+    }
   }
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -114,3 +114,46 @@ def test_dense_bf16_tensor_core_recheck_queue_overflow():
     X = workloads.iid(300, 512, seed=15, device="cpu", dtype=torch.bfloat16).cuda()
     stats, _ = compare_hash(dict(kind="e2lsh", d=512, m=32, L=8, w=1e-4, seed=4, compute=1), X)
     assert stats["n_flagged"] >= 0.9 * 300 * 256
+
+
+def _fp8_compare(kind, n, d, m, L, seed, X=None):
+    """Per-row-scaled FP8 rows and an FP8 family: the tcgen05 kind::f8f6f4
+    path against the oracle (projection = scale x projection of the E4M3
+    values), codes and keys bit for bit, projections within 1e-5."""
+    import oracle
+    if X is None:
+        X = workloads.iid(n, d, seed=seed, device="cpu")
+    q, scale = workloads.fp8_rows(X)
+    fam = lsh.Family(kind, d, m, L, w=4.0, seed=seed, compute=lsh.FP8_E4M3)
+    out = fam.hash(q.cuda(), codes=True, keys=True, proj=True, stats=True, row_scale=scale.cuda())
+    of = oracle.family(kind, d, m, L, w=4.0, seed=seed, compute=oracle.E4M3)
+    st, y, codes, keys = oracle.hash_dense(of, q.numpy(), dtype=oracle.E4M3, row_scale=scale.numpy())
+    assert st == 0
+    gc = out["codes"].cpu().numpy()
+    if fam.is_srp:
+        from gpu_helpers import unpack_bits
+        gc = unpack_bits(gc, m)
+    assert np.array_equal(gc, codes), np.argwhere(gc != codes)[:5]
+    assert np.array_equal(out["keys"].cpu().numpy().view(np.uint64), keys)
+    gp = out["proj"].cpu().numpy().astype(np.float64)
+    # the tolerance of every dense path: 1e-5 relative to max(|y|, ||x||), x = scale q
+    xn = np.linalg.norm(q.view(torch.float8_e4m3fn).to(torch.float64).numpy(), axis=1) * scale.numpy()
+    tol = np.maximum(np.abs(y), xn[:, None, None])
+    assert np.all(np.abs(gp - y) <= 1e-5 * tol), float(np.max(np.abs(gp - y) / tol))
+    fam.close()
+    return out["stats"]
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 1024, 64, 2), (20000, 256, 32, 8)])
+def test_dense_fp8_tensor_core_parity(kind, n, d, m, L):
+    st = _fp8_compare(kind, n, d, m, L, seed=n + d)
+    assert st["n_changed"] <= st["n_flagged"]
+
+
+def test_dense_fp8_rows_with_tiny_and_zero_rows():
+    X = workloads.iid(400, 256, seed=77, device="cpu")
+    X[3] = 0
+    X[5] *= 1e-30
+    X[7] *= 1e4
+    _fp8_compare("e2lsh", 400, 256, 16, 8, seed=5, X=X)

@@ -241,3 +241,52 @@ def test_decoders(orc):
     ok = np.isfinite(e4)
     assert np.array_equal(got[ok], e4[ok])
     assert np.isnan(got[~ok]).all()
+
+
+def test_round_e4m3_matches_torch_and_hand_values(orc):
+    """The oracle's E4M3 rounding (written from the format) against torch's
+    float8_e4m3fn conversion, and hand values: ties to even in the normal and
+    subnormal ranges, carries into the next binade, saturation."""
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(20000), rng.standard_normal(2000) * 1e-2,
+                        rng.uniform(-440, 440, 2000), np.ldexp(rng.integers(1, 64, 500), -10)]).astype(np.float32)
+    want = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([orc.round_e4m3(float(x)) for x in v])
+    assert np.array_equal(got, want)
+    hand = {0.0: 0.0, 2.0 ** -10: 0.0, 3 * 2.0 ** -10: 2.0 ** -8, 2.0 ** -9: 2.0 ** -9,
+            1.0625: 1.0, 1.1875: 1.25, 1.96875: 2.0, 240.0: 240.0, 248.0: 256.0, 447.0: 448.0,
+            1000.0: 448.0, -1.0625: -1.0, 2.0 ** -6 + 2.0 ** -10: 2.0 ** -6}
+    for x, y in hand.items():
+        assert orc.round_e4m3(x) == y, (x, orc.round_e4m3(x), y)
+
+
+def test_fp8_family_is_the_rounded_fp32_family(orc):
+    f32 = orc.family("e2lsh", 64, 8, 3, seed=9)
+    f8 = orc.family("e2lsh", 64, 8, 3, seed=9, compute=orc.E4M3)
+    want = torch.from_numpy(f32.G).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    assert np.array_equal(f8.G, want)
+    assert np.array_equal(f8.b, f32.b) and np.array_equal(f8.ka, f32.ka)
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp", "cs_e2lsh", "hcs_srp"])
+def test_fp8_rows_project_as_scale_times_projection(orc, kind):
+    """A per-row-scaled FP8 row projects to scale x (projection of its FP8
+    values): with small-integer FP8 values and an FP8 G the inner sums are
+    exact, so y must equal scale * (Q @ G) (or * S q) bit for bit."""
+    rng = np.random.default_rng(6)
+    d, m, L, n = 32, 8, 2, 7
+    dims = [4, 8] if kind.startswith("hcs") else None
+    mdims = [2, 4] if dims else None
+    fam = orc.family(kind, d, m, L, seed=12, dims=dims, mdims=mdims,
+                     compute=orc.E4M3 if kind in ("e2lsh", "srp") else orc.F32)
+    qv = rng.integers(-6, 7, size=(n, d)).astype(np.float32)
+    q8 = torch.from_numpy(qv).to(torch.float8_e4m3fn)
+    assert torch.equal(q8.to(torch.float32), torch.from_numpy(qv))
+    scale = (rng.uniform(0.1, 3.0, n)).astype(np.float32)
+    st, y, _, _ = orc.hash_dense(fam, q8.view(torch.uint8).numpy(), dtype=orc.E4M3, row_scale=scale)
+    assert st == 0
+    st0, y0, _, _ = orc.hash_dense(fam, qv, dtype=orc.F32)
+    if kind in ("e2lsh", "srp"):
+        ref = qv.astype(np.float64) @ fam.G.astype(np.float64)          # exact: small sums of FP8 products
+        assert np.array_equal(y0.reshape(n, -1), ref)
+    assert np.array_equal(y, scale.astype(np.float64)[:, None, None] * y0)
