@@ -309,8 +309,9 @@ def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
 
 def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
     """4,000,000 x 512 BF16 rows, m = 32, L = 64: dense E2LSH on the tensor cores
-    (GEMM 4M x 512 x 2048, BF16 family) with the FP64 boundary recheck, the same
-    family on the FP32 SIMT GEMM (bounded sample), and CS/HCS-E2LSH."""
+    (GEMM 4M x 512 x 2048, BF16 family, and per-row-scaled FP8 rows with an E4M3
+    family) with the exact boundary recheck, the BF16 family on the FP32 SIMT
+    GEMM (bounded sample), and CS/HCS-E2LSH."""
     import torch
     from paper_2503_06737_gb300 import lsh, workloads
     wl = workloads.WORKLOADS["iid_4M_d512_bf16"]
@@ -341,6 +342,21 @@ def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
                                  "tensor_frac": flops / (tms / 1e3) / 1e12 / bf16_peak,
                                  "flagged_per_entry": st["n_flagged"] / st["n_entries"],
                                  "mismatch_before_recheck": st["n_changed"] / st["n_entries"]}
+    # per-row-scaled FP8 rows (scale = row amax / 448) with an E4M3 family on the tensor cores
+    q8, sc8 = workloads.fp8_rows(X)
+    f8 = lsh.Family("e2lsh", d, m, L, w=wl["w"], seed=42, compute=lsh.FP8_E4M3)
+    m8 = lsh.dense_matrix(q8, sc8)
+    fms = timed(f8, 5, m8)
+    st8 = f8.hash(q8, keys=True, stats=True, row_scale=sc8)["stats"]
+    out["dense_fp8_tcgen05"] = {"hash_ms": fms, "points_per_s": n / (fms / 1e3),
+                                "tflops": flops / (fms / 1e3) / 1e12,
+                                "tensor_frac_of_bf16_peak": flops / (fms / 1e3) / 1e12 / bf16_peak,
+                                "flagged_per_entry": st8["n_flagged"] / st8["n_entries"],
+                                "mismatch_before_recheck": st8["n_changed"] / st8["n_entries"],
+                                "input": "E4M3 codes + FP32 row scale (2.05 GB)"}
+    log(f"tcgen05 dense FP8: {fms:.3f} ms")
+    f8.close()
+    del q8, sc8, m8
     # the same BF16 family on the FP32 SIMT GEMM, on a 131,072-row sample (strided view forces that path)
     ns = 131072
     Xpad = torch.zeros((ns, d + 4), dtype=torch.bfloat16, device=dev)
@@ -540,7 +556,13 @@ def main():
                              "achieved_gbs": bytes_alg / (hash_ms / 1e3) / 1e9,
                              "peak_gbs": peaks["hbm_gbs"],
                              "frac": bytes_alg / (hash_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                             "peak_source": peak_src}}
+                             "peak_source": peak_src},
+                # one 4-byte x operand from shared memory per (coordinate, table):
+                # 128 B/clk/SM of shared-memory return = 32 operands per clock per SM
+                "smem_operand_view": {"achieved_per_s": adds / (hash_ms / 1e3),
+                                      "peak_per_s": nsm * 32 * sm_max * 1e6,
+                                      "frac": adds / (hash_ms / 1e3) / (nsm * 32 * sm_max * 1e6),
+                                      "peak_source": f"{nsm} SMs x 32 x 4-byte operands/clk x {sm_max:.0f} MHz"}}
     t_wall2 = time.time()
 
     # ---- end to end through the public API with host buffers ----

@@ -204,8 +204,12 @@ void lsh_family_destroy(lsh_family_t fam);
  * Hash the rows of X for all L tables in one launch (Definitions 2, 3, 12,
  * 19, 25, 31).
  *   X      host pointer to the batch description; its arrays are device memory;
- *          X->d must equal the family's d.  Dense inputs: f32/bf16/f16 for the
- *          CS/HCS kinds.  CSR inputs: CS/HCS kinds.
+ *          X->d must equal the family's d.  Dense inputs: f32/bf16/f16 for every
+ *          kind; BF16 rows with a BF16 family, and per-row-scaled FP8 E4M3 rows
+ *          with an E4M3 family, go to the tensor cores (the projection of an FP8
+ *          row is its scale times the projection of its E4M3 values; FP8 rows
+ *          need an E4M3 family, d and ld multiples of 16, 8 <= m <= 64 dividing
+ *          64, m*L a multiple of 128, d <= 1024).  CSR inputs: CS/HCS kinds.
  *   codes  device, optional: E2LSH kinds int32 [n][L][m]; SRP kinds uint64
  *          [n][L][ceil(m/64)] with code l in bit (l % 64) of word l / 64.
  *   keys   device, optional: uint64 [L][n], the bucket key of (point, table):
@@ -216,6 +220,13 @@ void lsh_family_destroy(lsh_family_t fam);
  *   stats  host, optional: if given the call synchronises and fills it, and
  *          returns LSH_ENONFINITE / LSH_ERANGE when such rows/codes occurred.
  * Rows that hold NaN/Inf get key 0xFFFFFFFFFFFFFFFF and code INT32_MIN.
+ * Stream-ordered and asynchronous, with two exceptions: the first dense-row
+ * CS/HCS call of a shape (device, kind, d, m, L, modes, dtype) with at least
+ * 131,072 rows times the candidate tile plans of the hashing kernel on its
+ * first 131,072 rows and waits for them (once per shape; skipped while the
+ * stream is captured); and calls with stats synchronise.  Temporaries (the
+ * recheck queues of batches of 8,192 rows or more and of tensor-core calls)
+ * come from the device's stream-ordered memory pool.
  */
 lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys,
                     float *proj, lsh_hash_stats *stats, void *stream);

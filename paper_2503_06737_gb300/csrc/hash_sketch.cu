@@ -37,6 +37,10 @@
 //     FP64 from the same staged tile, in ascending j, one IEEE rounding per
 //     operation: the canonical value of Definitions 12/19/25/31.
 #include <algorithm>
+#include <cstring>
+#include <vector>
+#include <mutex>
+#include <map>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -579,6 +583,54 @@ int align16(int v) { return (v + 15) & ~15; }
 // Entry width: 16-bit byte offsets while 4 (d + 1) fits, else 32-bit.
 int entry_bytes(int d) { return 4 * (d + 1) < 65536 ? 2 : 4; }
 
+// The shared-memory layout of one plan: RG row groups of 32 rows, WPT warps
+// per table, table groups of (balanced) size <= Lg.  smem > kMaxSmem when it
+// does not fit.
+Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
+  const int G = (L + Lg - 1) / Lg;
+  const int Lgb = (L + G - 1) / G;  // balanced group size
+  Plan pl{};
+  pl.Lg = Lgb;
+  pl.G = G;
+  pl.RG = RG;
+  pl.WPT = WPT;
+  const int tasks = RG * Lgb * WPT;
+  int W = tasks < 32 ? tasks : 32;
+  if (tasks > 32) {
+    for (int w = 32; w >= 16; --w)
+      if (tasks % w == 0) {
+        W = w;
+        break;
+      }
+  }
+  if (W < 4) W = 4;
+  pl.W = W;
+  pl.x_stride = d + 1;
+  pl.cap = cap;
+  const int R = RG * kWarp;
+  int off = 0;
+  pl.off_ent = off;
+  off = align16(off + Lgb * cap * entry_bytes(d));
+  pl.off_seg = off;
+  off = align16(off + Lgb * m * 8);
+  pl.off_cst = off;
+  off = align16(off + Lgb * m * 16);
+  pl.off_key = off;
+  off = align16(off + R * Lgb * 8);
+  pl.off_x = off;
+  const int xbytes = R * (d + 1) * 4;
+  const int scratch = W * 2 * m * 4;
+  off = align16(off + (xbytes > scratch ? xbytes : scratch));
+  pl.off_xmax = off;
+  off = align16(off + R * 4);
+  pl.off_bad = off;
+  off = align16(off + R * 4);
+  pl.smem = off;
+  return pl;
+}
+
+// The default plan: most rows per tile, then two warps per table, then the
+// largest table group that fits.
 Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   Plan best{};
   best.smem = -1;
@@ -586,49 +638,37 @@ Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   for (int RG = 4; RG >= 1; RG >>= 1) {
     const int64_t ntiles = (n + RG * kWarp - 1) / (RG * kWarp);
     if (RG > 1 && ntiles < 2 * sms) continue;  // keep every SM busy twice over
-    for (int WPT = 2; WPT >= 1; --WPT) {
+    for (int WPT = 2; WPT >= 1; --WPT)
       for (int Lg = (L < 32 ? L : 32); Lg >= 1; --Lg) {
-        const int G = (L + Lg - 1) / Lg;
-        const int Lgb = (L + G - 1) / G;  // balanced group size
-        Plan pl{};
-        pl.Lg = Lgb;
-        pl.G = G;
-        pl.RG = RG;
-        pl.WPT = WPT;
-        const int tasks = RG * Lgb * WPT;
-        int W = tasks < 32 ? tasks : 32;
-        if (tasks > 32) {
-          for (int w = 32; w >= 16; --w)
-            if (tasks % w == 0) { W = w; break; }
-        }
-        if (W < 4) W = 4;
-        pl.W = W;
-        pl.x_stride = d + 1;
-        pl.cap = cap;
-        const int R = RG * kWarp;
-        int off = 0;
-        pl.off_ent = off;
-        off = align16(off + Lgb * cap * entry_bytes(d));
-        pl.off_seg = off;
-        off = align16(off + Lgb * m * 8);
-        pl.off_cst = off;
-        off = align16(off + Lgb * m * 16);
-        pl.off_key = off;
-        off = align16(off + R * Lgb * 8);
-        pl.off_x = off;
-        const int xbytes = R * (d + 1) * 4;
-        const int scratch = W * 2 * m * 4;
-        off = align16(off + (xbytes > scratch ? xbytes : scratch));
-        pl.off_xmax = off;
-        off = align16(off + R * 4);
-        pl.off_bad = off;
-        off = align16(off + R * 4);
-        pl.smem = off;
-        if (off <= kMaxSmem) return pl;
+        const Plan pl = plan_of(d, m, L, cap, RG, WPT, Lg);
+        if (pl.smem <= kMaxSmem) return pl;
+      }
+  }
+  return best;
+}
+
+// Candidate plans for the autotuner: for each row-group count and warps per
+// table, the largest fitting table group and the next smaller group count.
+std::vector<Plan> plan_candidates(int d, int m, int L, int cap, int64_t n) {
+  std::vector<Plan> out;
+  const int sms = num_sms();
+  for (int RG = 4; RG >= 1; RG >>= 1) {
+    const int64_t ntiles = (n + RG * kWarp - 1) / (RG * kWarp);
+    if (RG > 1 && ntiles < 2 * sms) continue;
+    for (int WPT = 4; WPT >= 1; WPT >>= 1) {
+      if (WPT > m) continue;
+      int found = 0, lastG = -1;
+      for (int Lg = (L < 32 ? L : 32); Lg >= 1 && found < 2; --Lg) {
+        const Plan pl = plan_of(d, m, L, cap, RG, WPT, Lg);
+        if (pl.smem > kMaxSmem || pl.G == lastG) continue;
+        if (pl.RG * pl.Lg * pl.WPT > 1024 / kWarp * 4) continue;
+        lastG = pl.G;
+        out.push_back(pl);
+        ++found;
       }
     }
   }
-  return best;
+  return out;
 }
 
 template <bool SRP, int DT, typename EntT>
@@ -810,17 +850,17 @@ cudaError_t launch_sketch_recheck(const SketchLaunch &p, const uint16_t *mlist, 
   }
 }
 
-cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {
-  if (p.n <= 0) return cudaSuccess;
+namespace {
+
+cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stream) {
   Args a{};
   a.p = p;
-  a.pl = make_plan(p.d, p.m, p.L, p.cap, p.n);
-  if (a.pl.smem <= 0) return cudaErrorInvalidConfiguration;
-  const int R = a.pl.RG * kWarp;
+  a.pl = pl;
+  const int R = pl.RG * kWarp;
   const int64_t ntiles = (p.n + R - 1) / R;
   if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
   a.ntiles = int(ntiles);
-  const int64_t cap = int64_t(num_sms()) / a.pl.G;
+  const int64_t cap = int64_t(num_sms()) / pl.G;
   int64_t slots = cap < ntiles ? cap : ntiles;
   if (slots < 1) slots = 1;
   a.slots = int(slots);
@@ -834,5 +874,92 @@ cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {
     default: return cudaErrorInvalidValue;
   }
 }
+
+// Autotuner: the first batch of at least kTuneRows rows of a shape (device,
+// kind, d, m, L, modes, dtype) times every candidate plan on its first
+// kTuneRows rows -- keys only, no recheck queue, into the caller's key buffer,
+// which the real launch then overwrites -- and keeps the fastest.  It is
+// skipped while the stream is being captured (the default plan is used).
+constexpr int64_t kTuneRows = 131072;
+
+struct TuneKey {
+  int dev, kind, d, m, L, N, dtype, cap;
+  int dims[LSH_MAX_MODES], mdims[LSH_MAX_MODES];
+  bool operator<(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) < 0; }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Plan> g_tuned;
+
+Plan tuned_plan(const SketchLaunch &p, cudaStream_t stream) {
+  const Plan dflt = make_plan(p.d, p.m, p.L, p.cap, p.n);
+  if (p.n < kTuneRows || dflt.smem <= 0) return dflt;
+  TuneKey key;
+  std::memset(&key, 0, sizeof(key));
+  cudaGetDevice(&key.dev);
+  key.kind = p.kind;
+  key.d = p.d;
+  key.m = p.m;
+  key.L = p.L;
+  key.N = p.N;
+  key.dtype = p.dtype;
+  key.cap = p.cap;
+  for (int k = 0; k < p.N && k < LSH_MAX_MODES; ++k) {
+    key.dims[k] = p.dims[k];
+    key.mdims[k] = p.mdims[k];
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return dflt;
+  SketchLaunch q = p;
+  q.n = kTuneRows;
+  q.codes = nullptr;
+  q.bits = nullptr;
+  q.proj = nullptr;
+  q.counters = nullptr;
+  q.queue = nullptr;
+  q.qcount = nullptr;
+  q.qcap = 0;
+  const std::vector<Plan> cands = plan_candidates(p.d, p.m, p.L, p.cap, kTuneRows);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return dflt;
+  }
+  Plan best = dflt;
+  float best_ms = 1e30f;
+  for (const Plan &pl : cands) {
+    if (launch_plan(q, pl, stream) != cudaSuccess) continue;  // warm-up (and attribute setting)
+    cudaEventRecord(e0, stream);
+    bool ok = launch_plan(q, pl, stream) == cudaSuccess;
+    cudaEventRecord(e1, stream);
+    float ms = 0.f;
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = pl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();  // a candidate that failed to launch leaves no sticky error
+  // tuned on kTuneRows rows: keep the row-group choice valid for the real n
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = best;
+  return best;
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {
+  if (p.n <= 0) return cudaSuccess;
+  const Plan pl = tuned_plan(p, stream);
+  if (pl.smem <= 0 || pl.smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+  return launch_plan(p, pl, stream);
+}
+
 
 }  // namespace lsh

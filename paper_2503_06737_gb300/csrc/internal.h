@@ -184,12 +184,13 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float 
 // (query_split: more CTAs per query for small batches) whose lists the last
 // CTA merges.  scratch: query_scratch_bytes(scratch_q, k) bytes, its first
 // scratch_q words zero (the kernel leaves them zero); NULL means G = 1.
+// q_live: optional device word; rows >= *q_live are padding and skipped.
 int query_split(int64_t q, int32_t k);
 size_t query_scratch_bytes(int64_t q_max, int32_t k);
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
                          const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
                          float *out_dist, unsigned long long *counters, void *scratch, int64_t scratch_q,
-                         cudaStream_t stream);
+                         const int64_t *q_live, cudaStream_t stream);
 
 // Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
 // Allocates its temporaries with cudaMallocAsync on `stream`.

@@ -656,7 +656,7 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
   else st = cuda_fail(e, "lsh_query temporaries");
   if (st == LSH_OK && idx->n > 0) {
     e = launch_query(qkeys, q, d.L, k, kind_is_srp(d.kind) ? 1 : 0, d.d, Q->values, Q->dtype, Q->ld, idx, ids,
-                     dist, cnt, qscratch, q, stream);
+                     dist, cnt, qscratch, q, nullptr, stream);
     if (e != cudaSuccess) st = cuda_fail(e, "lsh_query launch");
     else count_launches(1);
   } else if (st == LSH_OK) {

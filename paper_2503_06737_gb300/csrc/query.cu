@@ -55,6 +55,7 @@ struct QueryArgs {
   // split queries: G CTAs per query, each a share of the chunks; partial
   // lists pd/pi [q][G][k]; done[q] counts finished CTAs (the last merges and
   // resets it to 0)
+  const int64_t *q_live;   // optional device word: rows >= *q_live are padding, skipped
   int32_t G;
   float *pd;
   uint32_t *pi;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
 
   const int64_t qi = blockIdx.x / a.G;
   const int g = int(blockIdx.x % a.G);
+  if (a.q_live && qi >= *a.q_live) return;  // a padding row of a fixed-size batch
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int L = a.L, k = a.k, d = a.d;
 
@@ -467,7 +469,7 @@ size_t query_scratch_bytes(int64_t q_max, int32_t k) {
 cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k, int32_t metric, int32_t d,
                          const void *Q, int32_t q_dtype, int64_t q_ld, const lsh_index_s *idx, int32_t *out_ids,
                          float *out_dist, unsigned long long *counters, void *scratch, int64_t scratch_q,
-                         cudaStream_t stream) {
+                         const int64_t *q_live, cudaStream_t stream) {
   if (q <= 0) return cudaSuccess;
   if (L > kMaxL || k > kMaxK) return cudaErrorInvalidValue;
   QueryArgs a{};
@@ -495,6 +497,7 @@ cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k,
   a.out_ids = out_ids;
   a.out_dist = out_dist;
   a.counters = counters;
+  a.q_live = q_live;
   a.G = scratch && q <= scratch_q ? query_split(q, k) : 1;
   if (a.G > 1) {
     // layout of query_scratch_bytes(scratch_q, k): done[scratch_q], then the two list arrays

@@ -54,6 +54,8 @@ struct Slot {
   int32_t *ids_d = nullptr;      // [max_batch][k]
   float *dist_d = nullptr;
   void *qscratch = nullptr;      // split-query lists (query_scratch_bytes(max_batch, k))
+  int64_t *qlive_d = nullptr;    // live rows of the batch in flight (device word) ...
+  int64_t *qlive_h = nullptr;    // ... copied from this pinned word inside the batch's graph
   unsigned char *Qh = nullptr;   // pinned staging
   int32_t *ids_h = nullptr;
   float *dist_h = nullptr;
@@ -130,8 +132,10 @@ lsh_status enqueue_batch(lsh_server_s *s, Slot &sl, int64_t rows, int32_t dtype)
   Q.values = sl.Qd;
   lsh_status st = hash_impl(s->idx->fam, &Q, nullptr, sl.qkeys, rows, nullptr, nullptr, sl.stream);
   if (st != LSH_OK) return st;
+  LSH_CUDA_TRY(cudaMemcpyAsync(sl.qlive_d, sl.qlive_h, sizeof(int64_t), cudaMemcpyHostToDevice, sl.stream));
   LSH_CUDA_TRY(launch_query(sl.qkeys, rows, d.L, s->cfg.k, kind_is_srp(d.kind) ? 1 : 0, d.d, sl.Qd, dtype, d.d,
-                            s->idx, sl.ids_d, sl.dist_d, nullptr, sl.qscratch, s->cfg.max_batch, sl.stream));
+                            s->idx, sl.ids_d, sl.dist_d, nullptr, sl.qscratch, s->cfg.max_batch, sl.qlive_d,
+                            sl.stream));
   if (!s->cfg.use_graphs) count_launches(1);
   LSH_CUDA_TRY(cudaMemcpyAsync(sl.ids_h, sl.ids_d, size_t(rows) * s->cfg.k * 4, cudaMemcpyDeviceToHost, sl.stream));
   LSH_CUDA_TRY(cudaMemcpyAsync(sl.dist_h, sl.dist_d, size_t(rows) * s->cfg.k * 4, cudaMemcpyDeviceToHost,
@@ -146,6 +150,7 @@ lsh_status launch_batch(lsh_server_s *s, int si, CallbackArg *cb) {
   Request &r = *sl.req;
   const lsh_family_desc &d = s->idx->fam->host.desc;
   std::memcpy(sl.Qh, r.data.data(), r.data.size());
+  *sl.qlive_h = r.q;  // rows beyond it (bucket padding) skip the query work
   lsh_status st = LSH_OK;
   if (s->cfg.use_graphs) {
     const int64_t b = bucket_of(r.q, s->cfg.max_batch);
@@ -264,6 +269,8 @@ void free_server(lsh_server_s *s) {
     cudaFree(sl.ids_d);
     cudaFree(sl.dist_d);
     cudaFree(sl.qscratch);
+    cudaFree(sl.qlive_d);
+    cudaFreeHost(sl.qlive_h);
     cudaFreeHost(sl.Qh);
     cudaFreeHost(sl.ids_h);
     cudaFreeHost(sl.dist_h);
@@ -310,6 +317,8 @@ lsh_status lsh_server_create(lsh_index_t idx, const lsh_server_config *cfg, lsh_
     if (e == cudaSuccess) e = cudaMalloc(&sl.dist_d, mb * cfg->k * 4);
     if (e == cudaSuccess) e = cudaMalloc(&sl.qscratch, query_scratch_bytes(cfg->max_batch, cfg->k));
     if (e == cudaSuccess) e = cudaMemset(sl.qscratch, 0, mb * 4);  // the per-query counters start at zero
+    if (e == cudaSuccess) e = cudaMalloc(&sl.qlive_d, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&sl.qlive_h, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMallocHost(&sl.Qh, mb * d.d * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.ids_h, mb * cfg->k * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.dist_h, mb * cfg->k * 4);
