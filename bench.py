@@ -116,6 +116,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def shard_seed(rank: int) -> int:
+    """Data seed of a rank's shard: every rank hashes its own rows (weak
+    scaling; the points are independent, so no data-path exchange)."""
+    return 1235 + rank
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (the job's time) via one all-reduce MAX."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(world: int, n_per_rank: int, ms: float) -> float:
+    """Points per second of the whole job: all ranks' points over the job's time."""
+    return world * n_per_rank / (ms / 1e3)
+
+
 def _source_sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -488,7 +510,7 @@ def main():
     peaks, peak_src = _peaks()
     wl, fam_args = _workload(args.workload, args.kind)
     n, d, L, m = wl["n"], wl["d"], fam_args["L"], fam_args["m"]
-    X = _make_X(wl, seed=1235 + rank, device=dev)
+    X = _make_X(wl, seed=shard_seed(rank), device=dev)
     x_gb = X.numel() * X.element_size() / 1e9
     fam = lsh.Family(**fam_args)
     idx = fam.build_index(X, keep_data=False)
@@ -522,11 +544,8 @@ def main():
     t_wall1 = time.time()
     launches = lsh.launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(world, n, ms)
     log(f"timed region: {ms:.3f} ms/step")
 
     # ---- dominant kernel alone: the hashing launch (keys only) ----
@@ -588,11 +607,8 @@ def main():
         e2e_step()
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "points/s",
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e = {"value": job_throughput(world, n, e2e_ms), "unit": "points/s",
            "h2d_bytes_per_step": int(X.numel() * X.element_size()), "d2h_bytes_per_step": int(L * 8),
            "ms_per_step": e2e_ms}
     del Xh, Xd
