@@ -396,8 +396,9 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
         const uint2 sg = S[l];
         const int qp = int(sg.y & 0xffffu), qn = int(sg.y >> 16);
         const EntT *Q = E + sg.x;
-        // two quads per iteration (eight loads in flight), then the odd quad
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        // two quads per iteration (eight loads in flight), then the odd quad;
+        // two accumulators per half (the FP32 error bound holds in any order)
+        float p0 = 0.f, p1 = 0.f;
         int q = 0;
 #pragma unroll 1
         for (; q + 2 <= qp; q += 2) {
@@ -406,22 +407,22 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
           load_quad(Q, q + 1, f);
           p0 += lds_f32(xr, e[0]);
           p1 += lds_f32(xr, e[1]);
-          p2 += lds_f32(xr, e[2]);
-          p3 += lds_f32(xr, e[3]);
+          p0 += lds_f32(xr, e[2]);
+          p1 += lds_f32(xr, e[3]);
           p0 += lds_f32(xr, f[0]);
           p1 += lds_f32(xr, f[1]);
-          p2 += lds_f32(xr, f[2]);
-          p3 += lds_f32(xr, f[3]);
+          p0 += lds_f32(xr, f[2]);
+          p1 += lds_f32(xr, f[3]);
         }
         if (q < qp) {
           uint32_t e[4];
           load_quad(Q, q, e);
           p0 += lds_f32(xr, e[0]);
           p1 += lds_f32(xr, e[1]);
-          p2 += lds_f32(xr, e[2]);
-          p3 += lds_f32(xr, e[3]);
+          p0 += lds_f32(xr, e[2]);
+          p1 += lds_f32(xr, e[3]);
         }
-        float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+        float n0 = 0.f, n1 = 0.f;
         q = qp;
 #pragma unroll 1
         for (; q + 2 <= qp + qn; q += 2) {
@@ -430,22 +431,22 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
           load_quad(Q, q + 1, f);
           n0 += lds_f32(xr, e[0]);
           n1 += lds_f32(xr, e[1]);
-          n2 += lds_f32(xr, e[2]);
-          n3 += lds_f32(xr, e[3]);
+          n0 += lds_f32(xr, e[2]);
+          n1 += lds_f32(xr, e[3]);
           n0 += lds_f32(xr, f[0]);
           n1 += lds_f32(xr, f[1]);
-          n2 += lds_f32(xr, f[2]);
-          n3 += lds_f32(xr, f[3]);
+          n0 += lds_f32(xr, f[2]);
+          n1 += lds_f32(xr, f[3]);
         }
         if (q < qp + qn) {
           uint32_t e[4];
           load_quad(Q, q, e);
           n0 += lds_f32(xr, e[0]);
           n1 += lds_f32(xr, e[1]);
-          n2 += lds_f32(xr, e[2]);
-          n3 += lds_f32(xr, e[3]);
+          n0 += lds_f32(xr, e[2]);
+          n1 += lds_f32(xr, e[3]);
         }
-        const float y = ((p0 + p1) + (p2 + p3)) - ((n0 + n1) + (n2 + n3));
+        const float y = (p0 + p1) - (n0 + n1);
         const uint4 c = C[l];
         const float A = __uint_as_float(c.y);
         if (SRP) {
@@ -477,12 +478,10 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
         } else {
           const float bl = __uint_as_float(c.x);
           const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
-          const float fl = floorf(tf);
-          const float fr = tf - fl;
-          const float dist = fminf(fr, 1.f - fr);
+          const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
           const float M = fmaf(A, xm, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
           const bool flag = valid && !isbad && !(dist > M && fabsf(tf) < 4194304.f);
-          int code = int(fl);
+          int code = __float2int_rd(tf);
           if (__any_sync(0xffffffffu, flag)) {
             if (!queue_bin(p, flag, row, t, l, code, lane) && flag) {
               const EntT *P = E + sg.x;
