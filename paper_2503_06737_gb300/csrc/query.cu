@@ -8,7 +8,8 @@
 //           keys of table t -> (start, count) of its bucket;
 //   gather  the union, flattened over tables, is processed in chunks of up
 //           to kCap ids staged in shared memory;
-//   dedup   each chunk is bitonic-sorted and compacted to distinct ids;
+//   dedup   each chunk's ids go through a shared-memory hash set; its
+//           occupied slots are the chunk's distinct ids;
 //   rerank  one thread per candidate: FP32 distance from the index's copy of
 //           the data row, read with independent 16-byte loads (Euclidean for
 //           E2LSH kinds, 1 - cos for SRP kinds);
@@ -30,6 +31,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kCap = 4096;  // candidate ids per chunk
+constexpr int kHashBits = 13, kHash = 1 << kHashBits;  // dedup set: twice the chunk
 constexpr int kMaxL = 128;
 constexpr int kMaxK = 256;
 
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
   float *cdist = reinterpret_cast<float *>(cand + kCap);           // [kCap]
   float *topd = cdist + kCap;                                      // [k]
   uint32_t *topi = reinterpret_cast<uint32_t *>(topd + kMaxK);     // [k]
+  uint32_t *hset = topi + kMaxK;                                   // [kHash]
   __shared__ uint32_t wsum[kThreads / 32 + 1];
   __shared__ float red_d[kThreads / 32];
   __shared__ uint32_t red_i[kThreads / 32];
@@ -140,46 +143,32 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
 
   for (uint32_t c0 = uint32_t(g) * kCap; c0 < C; c0 += uint32_t(a.G) * kCap) {
     const uint32_t cc = min(uint32_t(kCap), C - c0);
-    uint32_t P = 1;
-    while (P < cc) P <<= 1;
-    // gather the chunk (flat index over tables)
-    for (uint32_t f = tid; f < P; f += kThreads) {
-      uint32_t id = 0xffffffffu;
-      if (f < cc) {
-        const uint32_t g = c0 + f;
-        int lo = 0, hi = L;  // last t with pre[t] <= g
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (pre[mid] <= g) lo = mid; else hi = mid;
-        }
-        id = a.ids[int64_t(lo) * a.n + bstart[lo] + (g - pre[lo])];
+    // dedup through a shared-memory hash set (open addressing, load <= 1/2):
+    // the gather inserts every id of the chunk; the distinct ids are then the
+    // occupied slots (their order does not matter to the top-k merge)
+    for (uint32_t i = tid; i < kHash; i += kThreads) hset[i] = 0xffffffffu;
+    __syncthreads();
+    for (uint32_t f = tid; f < cc; f += kThreads) {
+      const uint32_t g = c0 + f;
+      int lo = 0, hi = L;  // last t with pre[t] <= g
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= g) lo = mid; else hi = mid;
       }
-      cand[f] = id;
+      const uint32_t id = a.ids[int64_t(lo) * a.n + bstart[lo] + (g - pre[lo])];
+      uint32_t slot = (id * 2654435761u) >> (32 - kHashBits);
+      for (uint32_t probe = 0; probe < kHash; ++probe) {
+        const uint32_t old = atomicCAS(&hset[slot], 0xffffffffu, id);
+        if (old == 0xffffffffu || old == id) break;
+        slot = (slot + 1) & (kHash - 1);
+      }
     }
     __syncthreads();
-    // bitonic sort of cand[0..P)
-    for (uint32_t size = 2; size <= P; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t i = tid; i < P; i += kThreads) {
-          const uint32_t j = i ^ stride;
-          if (j > i) {
-            const uint32_t x = cand[i], y = cand[j];
-            const bool up = (i & size) == 0;
-            if ((x > y) == up) {
-              cand[i] = y;
-              cand[j] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    // compact distinct ids into cdist (reused as u32) with a block scan
-    uint32_t *uq = reinterpret_cast<uint32_t *>(cdist);
-    const uint32_t per = (cc + kThreads - 1) / kThreads;
-    const uint32_t b0 = tid * per, b1 = min(cc, b0 + per);
+    // compact the occupied slots into cand with a block scan
+    const uint32_t per = kHash / kThreads;
+    const uint32_t b0 = tid * per, b1 = b0 + per;
     uint32_t cnt = 0;
-    for (uint32_t f = b0; f < b1; ++f) cnt += (f == 0 || cand[f] != cand[f - 1]) ? 1u : 0u;
+    for (uint32_t f = b0; f < b1; ++f) cnt += hset[f] != 0xffffffffu ? 1u : 0u;
     uint32_t s = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -200,12 +189,8 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
     __syncthreads();
     uint32_t pos = wsum[warp] + s - cnt;
     const uint32_t U = wsum[kThreads / 32];
-    __syncthreads();  // everyone has read cand boundaries' scan before uq is written
     for (uint32_t f = b0; f < b1; ++f)
-      if (f == 0 || cand[f] != cand[f - 1]) uq[pos++] = cand[f];
-    __syncthreads();
-    // move distinct ids to the front of cand, distances into cdist
-    for (uint32_t u = tid; u < U; u += kThreads) cand[u] = uq[u];
+      if (hset[f] != 0xffffffffu) cand[pos++] = hset[f];
     __syncthreads();
     uniq_total += U;
     uniq_max = max(uniq_max, U);
@@ -221,6 +206,10 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
                                                           base * (a.x_dtype == LSH_F32 ? 4 : 2));
         const int per = a.x_dtype == LSH_F32 ? 4 : 8;
         const int nv = d / per;
+        // four partial sums per candidate (independent FMA chains); the query
+        // row read from shared memory as float4 (a broadcast to the warp)
+        float acc4[4] = {0.f, 0.f, 0.f, 0.f}, xx4[4] = {0.f, 0.f, 0.f, 0.f};
+        const float4 *q4 = reinterpret_cast<const float4 *>(qv);
         for (int v0 = 0; v0 < nv; v0 += 8) {
           uint4 w[8];
 #pragma unroll
@@ -247,21 +236,29 @@ __global__ void __launch_bounds__(kThreads) query_kernel(const QueryArgs a) {
                 x[2 * e + 1] = f.y;
               }
             }
-            const int j0 = (v0 + t) * per;
+            const int j0 = (v0 + t) * per;  // a multiple of 4
+            float qj[8];
+            const float4 qa = q4[j0 / 4];
+            qj[0] = qa.x; qj[1] = qa.y; qj[2] = qa.z; qj[3] = qa.w;
+            if (per == 8) {
+              const float4 qb = q4[j0 / 4 + 1];
+              qj[4] = qb.x; qj[5] = qb.y; qj[6] = qb.z; qj[7] = qb.w;
+            }
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               if (e >= per) break;
-              const float qj = qv[j0 + e];
               if (a.metric == 0) {
-                const float df = qj - x[e];
-                acc = fmaf(df, df, acc);
+                const float df = qj[e] - x[e];
+                acc4[e & 3] = fmaf(df, df, acc4[e & 3]);
               } else {
-                acc = fmaf(qj, x[e], acc);
-                xx = fmaf(x[e], x[e], xx);
+                acc4[e & 3] = fmaf(qj[e], x[e], acc4[e & 3]);
+                xx4[e & 3] = fmaf(x[e], x[e], xx4[e & 3]);
               }
             }
           }
         }
+        acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
+        xx = (xx4[0] + xx4[1]) + (xx4[2] + xx4[3]);
       } else {
         for (int j = 0; j < d; ++j) {
           const float x = ld_elem(a.X, a.x_dtype, base + j);
@@ -508,7 +505,7 @@ cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k,
     a.pi = reinterpret_cast<uint32_t *>(sb + align16(scratch_q * 4) + align16(lists * 4));
     if (q * a.G * k > lists) a.G = 1;
   }
-  const int smem = d * 4 + (2 * kMaxL + 1) * 4 + kCap * 8 + kMaxK * 8;
+  const int smem = d * 4 + (2 * kMaxL + 1) * 4 + kCap * 8 + kMaxK * 8 + kHash * 4;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
