@@ -400,6 +400,81 @@ def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
     return out
 
 
+def m_sweep(X, e0, e1, stream):
+    """The paper's space/time-versus-m comparison (Sec. 6, Table 1) on the
+    1,000,000 x 960 mixture rows, L = 64: family bytes and hashing time (keys
+    only) of CS-E2LSH, HCS-E2LSH (8x10x12) and the dense baseline on the
+    tensor cores (BF16 copy of the rows and of G) as m grows."""
+    import torch
+    from paper_2503_06737_gb300 import lsh
+    n, d, L = X.shape[0], X.shape[1], 64
+    Xb = X.to(torch.bfloat16)
+    keys = torch.empty((L, n), dtype=torch.int64, device=X.device)
+    mtx, mtxb = lsh.dense_matrix(X), lsh.dense_matrix(Xb)
+    hcs_m = {16: [2, 2, 4], 32: [2, 4, 4], 64: [4, 4, 4], 128: [4, 4, 8]}
+
+    def timed(fam, mt, reps=5):
+        fam.hash_into(mt, None, lsh._ptr(keys), None)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fam.hash_into(mt, None, lsh._ptr(keys), None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"n": n, "d": d, "L": L, "rows": []}
+    for m in (16, 32, 64, 128):
+        row = {"m": m}
+        f = lsh.Family("cs_e2lsh", d, m, L, w=4.0, seed=42)
+        row["cs_ms"], row["cs_family_bytes"] = timed(f, mtx), L * d * 3
+        f.close()
+        f = lsh.Family("hcs_e2lsh", d, m, L, w=4.0, seed=42, dims=[8, 10, 12], mdims=hcs_m[m])
+        row["hcs_ms"], row["hcs_family_bytes"] = timed(f, mtx), L * (8 + 10 + 12) * 3
+        f.close()
+        if m <= 64:
+            f = lsh.Family("e2lsh", d, m, L, w=4.0, seed=42, compute=lsh.BF16)
+            row["dense_bf16_tcgen05_ms"], row["dense_family_bytes"] = timed(f, mtxb), d * m * L * 2
+            f.close()
+        out["rows"].append(row)
+        log(f"m sweep m={m}: {row}")
+    del Xb, keys
+    torch.cuda.empty_cache()
+    return out
+
+
+def recall_vs_L(dev):
+    """The paper's recall protocol (Sec. 6) on a synthetic stand-in: 200,000 x 960
+    Gist-shaped mixture rows, 100 queries (database rows + N(0, 0.05^2) noise),
+    exact top-50 by brute force; m = 8, L = 1, 5, 10, 20, 50; recall@50 and
+    distinct candidates per query of E2LSH / CS-E2LSH / HCS-E2LSH (8x10x12 ->
+    2x2x2, w = 32, a bin width of the order of the 50-NN distances) and SRP / CS-SRP / HCS-SRP."""
+    import numpy as np
+    import torch
+    from paper_2503_06737_gb300 import lsh, measure, workloads
+    X = workloads.gmm(200_000, 960, 64, seed=1239, device=dev)
+    Q, _ = workloads.noisy_queries(X, 100, 0.05, seed=8)
+    truth, _ = measure.exact_knn(X, Q, 50)
+    truth = truth.cpu().numpy()
+    out = {"n": 200_000, "d": 960, "m": 8, "k": 50, "queries": 100, "rows": []}
+    for kind in ("e2lsh", "cs_e2lsh", "hcs_e2lsh", "srp", "cs_srp", "hcs_srp"):
+        hcs = kind.startswith("hcs")
+        for Lt in (1, 5, 10, 20, 50):
+            fam = lsh.Family(kind, 960, 8, Lt, w=32.0, seed=42, dims=[8, 10, 12] if hcs else None,
+                             mdims=[2, 2, 2] if hcs else None)
+            idx = fam.build_index(X, keep_data=True)
+            res = idx.query(Q, k=50, stats=True)
+            rec = measure.recall_at_k(res["ids"].cpu().numpy(), truth)
+            out["rows"].append({"kind": kind, "L": Lt, "recall50": rec,
+                                "cand_per_query": res["stats"]["n_unique"] / 100.0})
+            idx.close()
+            fam.close()
+    log("recall vs L done")
+    del X, Q
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=5e6, seconds_per_load=8.0):
     """Serving workload: 10,000,000 x 128 FP16 points from a 1,024-component
     mixture resident on the GPU; HCS-E2LSH (8 x 16 -> 4 x 4, m = 16) and
@@ -638,6 +713,11 @@ def main():
         log("per-family hashing done")
         variants.update(extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream))
         log("extra variants done")
+        del keys
+        torch.cuda.empty_cache()
+        variants["m_sweep_gmm64_1M_d960"] = m_sweep(X, e0, e1, stream)
+        keys = None
+        variants["recall_vs_L_gmm64_200k_d960"] = recall_vs_L(dev)
     if not args.no_serving and world == 1:
         idx.close()
         fam.close()

@@ -209,7 +209,7 @@ void lsh_family_destroy(lsh_family_t fam);
  *          with an E4M3 family, go to the tensor cores (the projection of an FP8
  *          row is its scale times the projection of its E4M3 values; FP8 rows
  *          need an E4M3 family, d and ld multiples of 16, 8 <= m <= 64 dividing
- *          64, m*L a multiple of 128, d <= 1024).  CSR inputs: CS/HCS kinds.
+ *          64, m*L a multiple of 128, d <= 16384).  CSR inputs: CS/HCS kinds.
  *   codes  device, optional: E2LSH kinds int32 [n][L][m]; SRP kinds uint64
  *          [n][L][ceil(m/64)] with code l in bit (l % 64) of word l / 64.
  *   keys   device, optional: uint64 [L][n], the bucket key of (point, table):

@@ -123,7 +123,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
   if (X->dtype == LSH_FP8_E4M3 && !(f->d_Gt8 && tc_dense_supported(d, X)))
     return fail(LSH_EUNSUPPORTED, "FP8 rows are hashed by dense families with an FP8 G on the tensor cores "
-                                  "(d and the row stride multiples of 16, m in 8..64 dividing 64, m*L a multiple of 128)");
+                                  "(d <= 16384 and the row stride multiples of 16, m in 8..64 dividing 64, m*L a multiple of 128)");
   SketchLaunch p{};
   p.X = X->values;
   p.row_scale = X->row_scale;

@@ -6,9 +6,10 @@
 //
 // Main kernel: persistent, one CTA per SM; CTA b owns the 128-row tiles
 // b, b + gridDim.x, ... and, for each, walks all 128-column projection tiles.
-//   warp 0   TMA loads (128-byte swizzle): the row tile's K slices once per
-//            row tile (resident in shared memory, d <= 512), the slices of G^T
-//            through a ring of SB stages;
+//   warp 0   TMA loads (128-byte swizzle): the row tile's K slices into 8
+//            slots -- once per row tile while they fit (d <= 512 BF16, 1024
+//            E4M3: the tile stays resident), else once per use, streamed --
+//            and the slices of G^T through a ring of SB stages;
 //   warp 1   tcgen05.mma kind::f16 (M = N = 128, K = 16, FP32 accumulate),
 //            issued by one elected lane of the converged warp;
 //   warps 2-17 drain the accumulators (tcgen05.ld) and run the epilogue.
@@ -325,6 +326,16 @@ __device__ __forceinline__ void recheck_block(const TcArgs &a, int64_t row, int 
   }
 }
 
+// Uses of row-tile slot z (z = kt when resident, kt % KMAX when streamed)
+// before the load for (local row tile mi, projection tile j, K tile kt):
+// resident slots are loaded once per row tile, streamed ones once per use.
+__device__ __forceinline__ uint32_t a_use(bool resident, uint32_t mi, int j, int kt, int ntn, int ktiles) {
+  if (resident) return mi;
+  const int z = kt % KMAX;
+  const uint32_t per_tile = uint32_t((ktiles - 1 - z) / KMAX + 1);  // uses of slot z per projection tile
+  return (mi * uint32_t(ntn) + uint32_t(j)) * per_tile + uint32_t(kt / KMAX);
+}
+
 // Persistent kernel: CTA b walks output tiles b, b + gridDim.x, ... (projection
 // tile fastest, so the CTAs running at one time share their X tiles in L2).
 // The accumulators are double buffered in TMEM: the MMA warp fills buffer
@@ -347,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int ntn = int(a.ML / BN);
   constexpr int kBKE = FP8 ? BKB : BKB / 2;  // K elements per tile (TMA coordinates are in elements)
+  const bool resident = a.ktiles <= KMAX;     // the row tile fits the KMAX slots
 
   if (threadIdx.x == 0) {
     aborted = 0;
@@ -385,13 +397,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
       for (int j = 0; j < ntn && ok; ++j) {
         const int n0 = ((rot + j) % ntn) * BN;
         for (int kt = 0; kt < a.ktiles; ++kt, ++it) {
-          if (j == 0) {
-            // slot kt is free once the last MMA of the previous row tile on it completed
-            if (__any_sync(0xffffffffu, aborted != 0) || (mi >= 1 && !mbar_wait_warp(&aempty[kt], (mi - 1) & 1))) {
+          // the row tile's K slice kt lives in slot z; resident rows load it once
+          // per row tile, streamed rows (d too large) for every projection tile
+          const int z = resident ? kt : kt % KMAX;
+          if (!resident || j == 0) {
+            const uint32_t u = a_use(resident, mi, j, kt, ntn, a.ktiles);  // uses of slot z before this one
+            // the slot is free once the MMA of its previous use completed
+            if (__any_sync(0xffffffffu, aborted != 0) || (u >= 1 && !mbar_wait_warp(&aempty[z], (u - 1) & 1))) {
               ok = false;
               break;
             }
-            tma_2d_elect(sA + kt * TILE_A, &mapA, &afull[kt], TILE_A, kt * kBKE, m0);
+            tma_2d_elect(sA + z * TILE_A, &mapA, &afull[z], TILE_A, kt * kBKE, m0);
           }
           if (__any_sync(0xffffffffu, aborted != 0) || (it >= SB && !mbar_wait_warp(&bempty[s], sph ^ 1))) {
             ok = false;
@@ -433,17 +449,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
         uint32_t dt = tmem + buf * (NCH * BN);
         int kc = 0;  // K tile within the current chunk
         for (int kt = 0; kt < a.ktiles; ++kt) {
-          if ((j == 0 && !mbar_wait_warp(&afull[kt], mi & 1)) || !mbar_wait_warp(&bfull[s], sph)) {
+          const int z = resident ? kt : kt % KMAX;
+          const uint32_t u = a_use(resident, mi, j, kt, ntn, a.ktiles);
+          if (((!resident || j == 0) && !mbar_wait_warp(&afull[z], u & 1)) || !mbar_wait_warp(&bfull[s], sph)) {
             ok = false;
             break;
           }
-          const uint64_t ad = adesc0 + uint64_t(kt * (TILE_A >> 4)), bd = bdesc0 + uint64_t(s * (TILE_B >> 4));
+          const uint64_t ad = adesc0 + uint64_t(z * (TILE_A >> 4)), bd = bdesc0 + uint64_t(s * (TILE_B >> 4));
           // four MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3 elements)
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             umma_elect<FP8>(dt, ad + uint64_t(2 * k), bd + uint64_t(2 * k), idesc, (kc == 0 && k == 0) ? 0u : 1u);
           commit_elect(&bempty[s]);
-          if (j == ntn - 1) commit_elect(&aempty[kt]);
+          if (!resident || j == ntn - 1) commit_elect(&aempty[z]);
           if (++s == SB) {
             s = 0;
             sph ^= 1;
@@ -921,7 +939,7 @@ bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X) {
   if (fd.d % per != 0 || X->ld % per != 0 || (reinterpret_cast<uintptr_t>(X->values) & 15) != 0) return false;
   if (ML % BN != 0 || 64 % fd.m != 0) return false;  // a 32-column slice or a pair of them holds whole tables
   if (fp8 && fd.m < 8) return false;
-  if (fd.d > KMAX * (fp8 ? BKB : BKB / 2)) return false;  // the row tile stays resident in shared memory
+  if (fd.d > 16384) return false;  // larger rows stream their K slices; bounded for the scratch records
   if (X->n > (int64_t(1) << 31) - BM || (X->n + BM - 1) / BM > 2147483647) return false;
   return encode_fn() != nullptr;
 }

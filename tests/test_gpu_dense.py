@@ -57,7 +57,8 @@ def test_dense_index_and_query():
 
 
 @pytest.mark.parametrize("kind", ["e2lsh", "srp"])
-@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 960, 64, 2), (77, 64, 8, 32)])
+@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 960, 64, 2), (77, 64, 8, 32),
+                                     (700, 2048, 32, 8), (5000, 640, 16, 16)])  # d > 512: streamed row tiles
 def test_dense_bf16_tensor_core_parity(kind, n, d, m, L):
     """BF16 rows and a BF16 family: the tcgen05 path (TMA, TMEM K-chunk
     accumulators, fused epilogue) against the oracle, bit-exact."""
@@ -145,7 +146,8 @@ def _fp8_compare(kind, n, d, m, L, seed, X=None):
 
 
 @pytest.mark.parametrize("kind", ["e2lsh", "srp"])
-@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 1024, 64, 2), (20000, 256, 32, 8)])
+@pytest.mark.parametrize("n,d,m,L", [(300, 512, 32, 8), (129, 128, 16, 16), (1000, 1024, 64, 2), (20000, 256, 32, 8),
+                                     (500, 2048, 16, 8)])  # d = 2048: the row tile streams its K slices
 def test_dense_fp8_tensor_core_parity(kind, n, d, m, L):
     st = _fp8_compare(kind, n, d, m, L, seed=n + d)
     assert st["n_changed"] <= st["n_flagged"]
