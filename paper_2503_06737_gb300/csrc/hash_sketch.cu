@@ -170,20 +170,24 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *e
   }
 }
 
-// Four member offsets (bytes into the row) at quad q of a list.
-__device__ __forceinline__ void load_quad(const uint32_t *E, int q, uint32_t (&o)[4]) {
-  const uint4 v = reinterpret_cast<const uint4 *>(E)[q];
-  o[0] = v.x;
-  o[1] = v.y;
-  o[2] = v.z;
-  o[3] = v.w;
+// Explicit shared-space loads with 32-bit addresses (row tile and entries).
+__device__ __forceinline__ float lds_at(uint32_t saddr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(saddr));
+  return v;
 }
-__device__ __forceinline__ void load_quad(const uint16_t *E, int q, uint32_t (&o)[4]) {
-  const uint2 v = reinterpret_cast<const uint2 *>(E)[q];
-  o[0] = v.x & 0xFFFFu;
-  o[1] = v.x >> 16;
-  o[2] = v.y & 0xFFFFu;
-  o[3] = v.y >> 16;
+__device__ __forceinline__ void load_quad_s(uint32_t qaddr, bool u16, uint32_t (&o)[4]) {
+  if (u16) {
+    uint32_t x, y;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(qaddr));
+    o[0] = x & 0xFFFFu;
+    o[1] = x >> 16;
+    o[2] = y & 0xFFFFu;
+    o[3] = y >> 16;
+  } else {
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3])
+                 : "r"(qaddr));
+  }
 }
 
 __device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off) {
@@ -398,53 +402,58 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
         const EntT *Q = E + sg.x;
         // two quads per iteration (eight loads in flight), then the odd quad;
         // two accumulators per half (the FP32 error bound holds in any order)
+        constexpr bool kU16 = sizeof(EntT) == 2;
+        constexpr uint32_t kQuadBytes = 4 * sizeof(EntT);
+        const uint32_t xs_a = static_cast<uint32_t>(__cvta_generic_to_shared(xr));
+        uint32_t qa = static_cast<uint32_t>(__cvta_generic_to_shared(Q));
         float p0 = 0.f, p1 = 0.f;
         int q = 0;
 #pragma unroll 1
-        for (; q + 2 <= qp; q += 2) {
+        for (; q + 2 <= qp; q += 2, qa += 2 * kQuadBytes) {
           uint32_t e[4], f[4];
-          load_quad(Q, q, e);
-          load_quad(Q, q + 1, f);
-          p0 += lds_f32(xr, e[0]);
-          p1 += lds_f32(xr, e[1]);
-          p0 += lds_f32(xr, e[2]);
-          p1 += lds_f32(xr, e[3]);
-          p0 += lds_f32(xr, f[0]);
-          p1 += lds_f32(xr, f[1]);
-          p0 += lds_f32(xr, f[2]);
-          p1 += lds_f32(xr, f[3]);
+          load_quad_s(qa, kU16, e);
+          load_quad_s(qa + kQuadBytes, kU16, f);
+          p0 += lds_at(xs_a + e[0]);
+          p1 += lds_at(xs_a + e[1]);
+          p0 += lds_at(xs_a + e[2]);
+          p1 += lds_at(xs_a + e[3]);
+          p0 += lds_at(xs_a + f[0]);
+          p1 += lds_at(xs_a + f[1]);
+          p0 += lds_at(xs_a + f[2]);
+          p1 += lds_at(xs_a + f[3]);
         }
         if (q < qp) {
           uint32_t e[4];
-          load_quad(Q, q, e);
-          p0 += lds_f32(xr, e[0]);
-          p1 += lds_f32(xr, e[1]);
-          p0 += lds_f32(xr, e[2]);
-          p1 += lds_f32(xr, e[3]);
+          load_quad_s(qa, kU16, e);
+          qa += kQuadBytes;
+          p0 += lds_at(xs_a + e[0]);
+          p1 += lds_at(xs_a + e[1]);
+          p0 += lds_at(xs_a + e[2]);
+          p1 += lds_at(xs_a + e[3]);
         }
         float n0 = 0.f, n1 = 0.f;
-        q = qp;
+        q = 0;
 #pragma unroll 1
-        for (; q + 2 <= qp + qn; q += 2) {
+        for (; q + 2 <= qn; q += 2, qa += 2 * kQuadBytes) {
           uint32_t e[4], f[4];
-          load_quad(Q, q, e);
-          load_quad(Q, q + 1, f);
-          n0 += lds_f32(xr, e[0]);
-          n1 += lds_f32(xr, e[1]);
-          n0 += lds_f32(xr, e[2]);
-          n1 += lds_f32(xr, e[3]);
-          n0 += lds_f32(xr, f[0]);
-          n1 += lds_f32(xr, f[1]);
-          n0 += lds_f32(xr, f[2]);
-          n1 += lds_f32(xr, f[3]);
+          load_quad_s(qa, kU16, e);
+          load_quad_s(qa + kQuadBytes, kU16, f);
+          n0 += lds_at(xs_a + e[0]);
+          n1 += lds_at(xs_a + e[1]);
+          n0 += lds_at(xs_a + e[2]);
+          n1 += lds_at(xs_a + e[3]);
+          n0 += lds_at(xs_a + f[0]);
+          n1 += lds_at(xs_a + f[1]);
+          n0 += lds_at(xs_a + f[2]);
+          n1 += lds_at(xs_a + f[3]);
         }
-        if (q < qp + qn) {
+        if (q < qn) {
           uint32_t e[4];
-          load_quad(Q, q, e);
-          n0 += lds_f32(xr, e[0]);
-          n1 += lds_f32(xr, e[1]);
-          n0 += lds_f32(xr, e[2]);
-          n1 += lds_f32(xr, e[3]);
+          load_quad_s(qa, kU16, e);
+          n0 += lds_at(xs_a + e[0]);
+          n1 += lds_at(xs_a + e[1]);
+          n0 += lds_at(xs_a + e[2]);
+          n1 += lds_at(xs_a + e[3]);
         }
         const float y = (p0 + p1) - (n0 + n1);
         const uint4 c = C[l];
