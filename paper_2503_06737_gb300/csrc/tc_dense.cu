@@ -110,8 +110,8 @@ __device__ __forceinline__ bool mbar_try_sleep(uint64_t *b, uint32_t parity, uin
 // The same wait by a whole warp, with a warp-uniform answer.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *b, uint32_t parity);
 // Bounded wait for the phase of the given parity: false after about two
-// seconds.  hint_ns > 0 lets the thread sleep between polls (for warps that
-// wait long, so that they leave the issue slots to the MMA thread).
+// seconds.  hint_ns > 0 lets the thread sleep between polls (it wakes when the
+// phase completes), so that waiting warps leave the issue slots to others.
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t hint_ns = 0) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtimer_ns();
@@ -122,7 +122,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t
   return false;
 }
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *b, uint32_t parity) {
-  return __all_sync(0xffffffffu, mbar_wait(b, parity));
+  // the waiting warp sleeps until the phase completes (or 1 us passes) rather
+  // than spinning on the issue slots the epilogue warps of its scheduler need
+  return __all_sync(0xffffffffu, mbar_wait(b, parity, 1000));
 }
 // One elected lane of a converged warp arms the barrier with the expected
 // bytes and issues the tile load (the predicate stays inside the asm, so the
