@@ -250,6 +250,19 @@ lsh_status lsh_build_index(lsh_family_t fam, const lsh_matrix *X, int32_t keep_d
  */
 lsh_status lsh_index_rebuild(lsh_index_t idx, const lsh_matrix *X, void *stream);
 
+/*
+ * The same rebuild from rows in HOST memory (X->values a host pointer, dense
+ * f32/bf16/f16 rows; pinned memory for full copy speed): the rows go to the
+ * device in chunks of chunk_rows (0: max(131072, n/16)) on a stream of the
+ * call's own while the previous chunk is hashed on `stream` -- the transfer
+ * and the hashing overlap -- then the tables are sorted on `stream`.  When the
+ * index keeps data the rows land in its copy, else in two staging buffers
+ * from the stream-ordered pool.  Returns once the work is enqueued; the
+ * caller must keep X's rows unchanged until `stream` has passed the call.
+ * Not for stream capture (it creates a stream and events).
+ */
+lsh_status lsh_index_rebuild_host(lsh_index_t idx, const lsh_matrix *X, int64_t chunk_rows, void *stream);
+
 /* n and, for each table, the number of buckets (host, [L]; may be NULL).  Synchronous. */
 lsh_status lsh_index_info(lsh_index_t idx, int64_t *n, int64_t *nbuckets);
 

@@ -604,6 +604,74 @@ lsh_status lsh_index_rebuild(lsh_index_t idx, const lsh_matrix *X, void *stream_
   return index_fill(idx, X, stream);
 }
 
+lsh_status lsh_index_rebuild_host(lsh_index_t idx, const lsh_matrix *X, int64_t chunk_rows, void *stream_) {
+  if (!idx || !X) return fail(LSH_EINVAL, "NULL argument");
+  if (X->rowptr) return fail(LSH_EINVAL, "host rebuild takes dense rows");
+  lsh_status st = validate_matrix(idx->fam, X, false);
+  if (st != LSH_OK) return st;
+  if (X->n != idx->n) return fail(LSH_EINVAL, "rebuild needs the same n as the index");
+  if (X->dtype == LSH_FP8_E4M3) return fail(LSH_EUNSUPPORTED, "host rebuild of FP8 rows is not supported");
+  if (idx->d_data && X->dtype != idx->data_dtype) return fail(LSH_EINVAL, "rebuild data must match the kept data");
+  if (chunk_rows < 0) return fail(LSH_EINVAL, "chunk_rows must be >= 0");
+  const int64_t n = X->n;
+  if (n == 0) return LSH_OK;
+  if (chunk_rows == 0) chunk_rows = std::max<int64_t>(131072, (n + 15) / 16);
+  chunk_rows = std::min(chunk_rows, n);
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int L = idx->L;
+  const size_t es = dtype_size(X->dtype), rowb = es * size_t(X->d);
+  keep_pool_warm();
+  // the rows stream to the device in chunks on a second stream while the
+  // previous chunk is hashed; into the index's data copy when it keeps one,
+  // else into two staging buffers used alternately
+  uint64_t *keys = nullptr;
+  void *stage[2] = {nullptr, nullptr};
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_start = nullptr, copied[2] = {nullptr, nullptr}, hashed[2] = {nullptr, nullptr};
+  auto release = [&]() {
+    if (keys) cudaFreeAsync(keys, stream);
+    for (int b = 0; b < 2; ++b)
+      if (stage[b]) cudaFreeAsync(stage[b], stream);
+    for (cudaEvent_t ev : {ev_start, copied[0], copied[1], hashed[0], hashed[1]})
+      if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+  };
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&keys), sizeof(uint64_t) * size_t(n) * L, stream);
+  for (int b = 0; b < 2 && e == cudaSuccess && !idx->d_data; ++b) e = cudaMallocAsync(&stage[b], rowb * chunk_rows, stream);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (cudaEvent_t *ev : {&ev_start, &copied[0], &copied[1], &hashed[0], &hashed[1]})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  // the copies start once the caller's stream has reached this call (buffers allocated)
+  if (e == cudaSuccess) e = cudaEventRecord(ev_start, stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+  int64_t c = 0;
+  for (int64_t r0 = 0; r0 < n && e == cudaSuccess && st == LSH_OK; r0 += chunk_rows, ++c) {
+    const int64_t rows = std::min(chunk_rows, n - r0);
+    const int b = int(c & 1);
+    void *dst = idx->d_data ? static_cast<char *>(idx->d_data) + rowb * size_t(r0) : stage[b];
+    if (!idx->d_data && c >= 2) e = cudaStreamWaitEvent(cs, hashed[b], 0);  // the buffer's previous chunk is hashed
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dst, rowb, static_cast<const char *>(X->values) + es * size_t(X->ld) * size_t(r0),
+                            es * size_t(X->ld), rowb, size_t(rows), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, copied[b], 0);
+    if (e != cudaSuccess) break;
+    lsh_matrix part = *X;
+    part.values = dst;
+    part.n = rows;
+    part.ld = X->d;
+    st = hash_impl(idx->fam, &part, nullptr, keys + r0, n, nullptr, nullptr, stream);
+    if (st == LSH_OK) e = cudaEventRecord(hashed[b], stream);
+  }
+  if (e == cudaSuccess && st == LSH_OK) {
+    e = build_tables(keys, n, L, idx->d_ids, idx->d_ukeys, idx->d_offsets, idx->d_nb, stream);
+  }
+  release();
+  if (st != LSH_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "lsh_index_rebuild_host");
+  return LSH_OK;
+}
+
 lsh_status lsh_index_info(lsh_index_t idx, int64_t *n, int64_t *nbuckets) {
   if (!idx) return fail(LSH_EINVAL, "NULL index");
   if (n) *n = idx->n;

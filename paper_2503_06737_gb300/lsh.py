@@ -97,6 +97,7 @@ SIGNATURES = [
     ("lsh_hash", ctypes.c_int, [P, ctypes.POINTER(Matrix), P, P, P, ctypes.POINTER(HashStats), P]),
     ("lsh_build_index", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, ctypes.POINTER(P), P]),
     ("lsh_index_rebuild", ctypes.c_int, [P, ctypes.POINTER(Matrix), P]),
+    ("lsh_index_rebuild_host", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int64, P]),
     ("lsh_index_info", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), P]),
     ("lsh_index_export", ctypes.c_int, [P, P, P, P, P]),
     ("lsh_query", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, P, P,
@@ -317,6 +318,11 @@ class Index:
 
     def rebuild_into(self, mtx: Matrix, stream=None):
         _check(lib().lsh_index_rebuild(self.handle, ctypes.byref(mtx), _stream(stream)))
+
+    def rebuild_from_host(self, X_host, chunk_rows=0, stream=None):
+        """Rebuild from a (pinned) host tensor: chunked copies overlap the hashing."""
+        mtx = dense_matrix(X_host)
+        _check(lib().lsh_index_rebuild_host(self.handle, ctypes.byref(mtx), int(chunk_rows), _stream(stream)))
 
     def info(self):
         import numpy as np

@@ -93,3 +93,25 @@ def test_full_size_index_invariants():
     ofam = oracle.family("hcs_e2lsh", 960, 64, L, w=4.0, seed=42, dims=wl["hcs_dims"], mdims=wl["hcs_mdims"])
     _, _, _, okeys = oracle.hash_dense(ofam, Xh, dtype=dt, want_y=False, want_codes=False)
     assert np.array_equal(keys[:, torch.as_tensor(rows, device="cuda")].cpu().numpy().view(np.uint64), okeys)
+
+
+@pytest.mark.parametrize("keep", [False, True])
+def test_rebuild_from_host_equals_device_rebuild(keep):
+    """Host rows streamed in chunks (copies overlapping the hashing) give the
+    same tables as a rebuild from the same rows on the device."""
+    X = workloads.gmm(300_000, 128, 16, seed=51, device="cpu")
+    Xh = X.pin_memory()
+    fam = lsh.Family("cs_e2lsh", 128, 16, 8, w=4.0, seed=52)
+    a = fam.build_index(X.cuda(), keep_data=keep)
+    b = fam.build_index(workloads.gmm(300_000, 128, 16, seed=53, device="cuda"), keep_data=keep)
+    b.rebuild_from_host(Xh, chunk_rows=70_000)  # ragged last chunk
+    torch.cuda.synchronize()
+    ea, eb = a.export(), b.export()
+    assert np.array_equal(ea["nb"], eb["nb"]) and np.array_equal(ea["ids"], eb["ids"])
+    for t, nb in enumerate(ea["nb"]):  # the arrays hold nb[t] buckets; the rest is unused
+        assert np.array_equal(ea["ukeys"][t, :nb], eb["ukeys"][t, :nb]), t
+        assert np.array_equal(ea["offsets"][t, :nb + 1], eb["offsets"][t, :nb + 1]), t
+    if keep:
+        Q = X[:50].cuda() + 0.01
+        ra, rb = a.query(Q, k=5), b.query(Q, k=5)
+        assert torch.equal(ra["ids"], rb["ids"]) and torch.equal(ra["dist"], rb["dist"])
