@@ -54,7 +54,7 @@ typedef enum {
   LSH_ECUDA = 3,         /* a CUDA runtime call failed */
   LSH_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
   LSH_ENONFINITE = 5,    /* an input row held NaN or Inf: its codes and keys are not defined */
-  LSH_EUNSUPPORTED = 6,  /* valid request this build does not implement */
+  LSH_EUNSUPPORTED = 6,  /* valid request the library does not implement */
   LSH_ERANGE = 7         /* an E2LSH code fell outside int32 */
 } lsh_status;
 
