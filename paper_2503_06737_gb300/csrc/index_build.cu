@@ -206,6 +206,10 @@ __global__ void __launch_bounds__(kThreads) seg_count(const uint64_t *__restrict
   if (threadIdx.x == 0) bcnt[int64_t(t) * ntiles + tile] = tot;
 }
 
+// Bucket heads of one tile, in order: warp w walks keys [w*512, (w+1)*512) of
+// the tile 32 at a time (lane = consecutive key: coalesced), counts its heads
+// with ballots, and after a block scan over the warps writes them with the
+// same ballots (order preserved inside the warp and across warps).
 __global__ void __launch_bounds__(kThreads) seg_write(const uint64_t *__restrict__ sk, int64_t n, int ntiles,
                                                       const uint32_t *__restrict__ boffs,
                                                       const int64_t *__restrict__ nb,
@@ -213,28 +217,39 @@ __global__ void __launch_bounds__(kThreads) seg_write(const uint64_t *__restrict
                                                       uint32_t *__restrict__ offsets) {
   __shared__ uint32_t wsum[33];
   const int t = blockIdx.y, tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t *k = sk + int64_t(t) * n;
-  const int64_t base = int64_t(tile) * kTile;
-  // contiguous chunk of kItems keys per thread keeps heads in order
-  const int64_t my = base + int64_t(threadIdx.x) * kItems;
-  uint32_t c = 0;
-#pragma unroll
+  const int64_t wbase = int64_t(tile) * kTile + int64_t(warp) * (kItems * 32);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t heads = 0;
+#pragma unroll 4
   for (int it = 0; it < kItems; ++it) {
-    const int64_t idx = my + it;
-    if (idx < n && (idx == 0 || k[idx] != k[idx - 1])) ++c;
+    const int64_t idx = wbase + it * 32 + lane;
+    const bool h = idx < n && (idx == 0 || k[idx] != k[idx - 1]);
+    heads += __popc(__ballot_sync(0xffffffffu, h));
   }
+  // block-exclusive scan of the per-warp head counts (one value per warp, lane 0)
   uint32_t tot;
-  uint32_t pos = boffs[int64_t(t) * ntiles + tile] + block_exclusive_scan(c, wsum, tot);
+  const uint32_t wpos = block_exclusive_scan(lane == 0 ? heads : 0u, wsum, tot);
+  uint32_t pos = boffs[int64_t(t) * ntiles + tile] + __shfl_sync(0xffffffffu, wpos, 0);
   uint64_t *uk = ukeys + int64_t(t) * n;
   uint32_t *of = offsets + int64_t(t) * (n + 1);
-#pragma unroll
+#pragma unroll 4
   for (int it = 0; it < kItems; ++it) {
-    const int64_t idx = my + it;
-    if (idx < n && (idx == 0 || k[idx] != k[idx - 1])) {
-      uk[pos] = k[idx];
-      of[pos] = uint32_t(idx);
-      ++pos;
+    const int64_t idx = wbase + it * 32 + lane;
+    uint64_t key = 0;
+    bool h = false;
+    if (idx < n) {
+      key = k[idx];
+      h = idx == 0 || key != k[idx - 1];
     }
+    const uint32_t bal = __ballot_sync(0xffffffffu, h);
+    if (h) {
+      const uint32_t p = pos + __popc(bal & lt);
+      uk[p] = key;
+      of[p] = uint32_t(idx);
+    }
+    pos += __popc(bal);
   }
   if (tile == 0 && threadIdx.x == 0) of[nb[t]] = uint32_t(n);
 }
