@@ -6,9 +6,10 @@
 //     tables are staged once in shared memory as per-table member lists: for
 //     each bin, the coordinates j < d with s = +1 (ascending j), then those
 //     with s = -1, each half padded to a multiple of four with the offset of
-//     the row's zero slot, every entry the byte offset 4j.  HCS lists are
-//     derived in the CTA from the per-mode tables h_k, s_k (the sign of j is
-//     prod_k s_k(i_k)), so HBM holds only O(N d^(1/N)) words per table.
+//     the row's zero slot, every entry the byte offset 4j (16-bit while
+//     4(d+1) < 2^16, else 32-bit).  HCS lists are derived in the CTA from the
+//     per-mode tables h_k, s_k (the sign of j is prod_k s_k(i_k)), so HBM
+//     holds only O(N d^(1/N)) words per table.
 //   * The row tile is read once from HBM with coalesced loads into a padded
 //     row-major tile (row stride d+1 words: lane r reading row r hits bank
 //     (r + j) mod 32, conflict free; word d is the zero slot).  The next tile
@@ -16,11 +17,12 @@
 //     groups that share a tile run concurrently, so it leaves HBM once.
 //   * Lane = row.  A table is split over WPT warps (bins l = k, k+WPT, ...),
 //     which gives the SM enough independent shared-memory loads in flight.
-//     Entries are read four at a time as warp-uniform 128-bit broadcasts; each
-//     x read is one conflict-free 32-bit load into one of four accumulators.
+//     Entries are read four at a time as warp-uniform broadcasts; each x read
+//     is one conflict-free 32-bit load into one of two accumulators per half.
 //     Partial keys of the warps of one table are combined in shared memory:
 //     the key fold is a sum mod 2^32 (E2LSH, SRP m > 64) or an OR of bits
-//     (SRP m <= 64), so partials combine exactly.
+//     (SRP m <= 64), so partials combine exactly.  The plan (RG, WPT, Lg) is
+//     autotuned per shape on the first large batch (see tuned_plan).
 //   * Exactness.  The FP32 sum of the k terms of a bin differs from the exact
 //     sum by at most gamma_{k-1} * sum|x_j| <= gamma_{k-1} * k * max|x|
 //     (Higham's bound, any summation order; zero padding adds no error), and
@@ -29,13 +31,17 @@
 //     y, b)) * fl(1/w)):
 //        |t - t_fp64| <= (sqrt(m)/w) E + 4.1u (sqrt(m)|y| + b)/w + 2.1u(|t|+1)
 //                     <= A max|x| + 10.2u |t| + 15.3u,
-//     using (sqrt(m)|y| + b)/w <= 1.0001 |t| + 2 (b < w), where u = 2^-24,
-//     A = 1.02 (sqrt(m)/w) gamma_{k-1}(1 + 2 gamma) k, and the last term also
-//     covers the rounding of fr = t - floor(t) and 1 - fr.  An entry whose t
-//     lies within that bound of an integer (E2LSH), or whose |y| is within
-//     A max|x| of 0 (SRP, A without sqrt(m)/w), is recomputed by its lane in
-//     FP64 from the same staged tile, in ascending j, one IEEE rounding per
-//     operation: the canonical value of Definitions 12/19/25/31.
+//     using (sqrt(m)|y| + b)/w <= 1.0001 |t| + 2 (b < w), where u = 2^-24 and
+//     A = 1.02 (sqrt(m)/w) gamma_{k-1}(1 + 2 gamma) k; the distance of t to the
+//     nearest integer is computed exactly.  A bin whose t lies within that
+//     bound of an integer (E2LSH), or whose |y| is within A max|x| of 0 (SRP,
+//     A without sqrt(m)/w), gets the canonical value of Definitions 12/19/25/31
+//     -- the ascending FP64 sum, one IEEE rounding per operation: large
+//     batches queue such bins for sketch_recheck_kernel, which patches codes,
+//     bits and keys; small batches (and queue overflow) recheck in place.
+//     Either way the value is computed exactly as an int64 sum on the least
+//     exponent grid of the bin's terms when that sum is exact in the FP64
+//     loop, else by the FP64 loop itself.
 #include <algorithm>
 #include <cstring>
 #include <vector>

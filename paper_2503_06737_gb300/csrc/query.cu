@@ -3,7 +3,8 @@
 // take the union of those buckets, rank the distinct candidates by exact
 // distance and keep the k best by (distance, id).
 //
-// One CTA per query, fused:
+// G CTAs per query (G = 1 for large batches, up to 32 for small ones: each
+// takes every G-th chunk, and the last to finish merges the G lists), fused:
 //   probe   thread t binary-searches the query's key in the sorted distinct
 //           keys of table t -> (start, count) of its bucket;
 //   gather  the union, flattened over tables, is processed in chunks of up

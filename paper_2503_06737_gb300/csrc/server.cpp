@@ -9,10 +9,12 @@
 // slot owns a stream, device buffers sized for the largest batch, pinned host
 // staging and, per power-of-two batch bucket, a captured CUDA graph of
 //   H2D(queries) -> hash (all L tables) -> probe/dedup/rerank -> D2H(results)
-// that later batches of that bucket replay (rows beyond the batch are padding
-// whose results are dropped).  A host callback on the stream marks the batch
-// done; latency runs from submit to results on the host.  Every query is
-// answered by its own CTA from its own row, so a result does not depend on
+// that later batches of that bucket replay (rows beyond the batch are padding:
+// the live row count is copied into the graph from a pinned word, and the
+// query CTAs of padding rows return at once).  A host callback on the stream
+// marks the batch done; latency runs from submit to results on the host.
+// Every query is answered from its own row by its own CTAs, whose merged list
+// does not depend on how many CTAs share it, so a result does not depend on
 // which requests share its batch or run beside it.
 #include <cuda_runtime.h>
 
