@@ -86,6 +86,7 @@ def test_null_arguments(L):
     assert lib.lsh_query(None, None, 10, None, None, None, None) == 1
     assert lib.lsh_family_export(None, None, None, None, None, None, None) == 1
     assert lib.lsh_index_export(None, None, None, None, None) == 1
+    assert lib.lsh_index_rebuild_host(None, None, 0, None) == 1
     lib.lsh_family_destroy(None)
     lib.lsh_index_destroy(None)
 
