@@ -275,6 +275,27 @@ def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
                                "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
                                "note": "FP32 SIMT GEMM x G (d x mL = %d x %d) + fused epilogue, same m*L" % (d, m * L)}
     fd.close()
+    # the same dense baseline on the tensor cores: BF16 copy of the rows, BF16 G
+    Xb = X.to(torch.bfloat16)
+    mtxb = lsh.dense_matrix(Xb)
+    fb = lsh.Family(**dict(fa, compute=lsh.BF16))
+    fb.hash_into(mtxb, None, lsh._ptr(keys), None)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        fb.hash_into(mtxb, None, lsh._ptr(keys), None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / 3
+    st = fb.hash(Xb[:65536], keys=True, stats=True)["stats"]
+    out["dense_bf16_tcgen05_e2lsh"] = {
+        "hash_ms": bms, "points_per_s": n / (bms / 1e3), "tflops": flops / (bms / 1e3) / 1e12,
+        "tensor_frac": flops / (bms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1900.0),
+        "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
+        "note": "tcgen05 BF16 x BF16 -> FP32 + exact recheck; BF16 copy of the rows (an input rounding the "
+                "CS/HCS paths do not make), same m*L"}
+    fb.close()
+    del Xb, mtxb
     # CSR workload: 200,000 x 20,000 at 1%, m = 256, L = 20
     cw = workloads.WORKLOADS["csr_200k_d20000"]
     rowptr, cols, vals = workloads.csr_rows(cw["n"], cw["d"], cw["nnz"], seed=1236, device=X.device)

@@ -83,8 +83,9 @@ struct lsh_family_s {
   float *d_gnorm = nullptr;       // [m*L] column norms, rounded up
   uint16_t *d_Gt16 = nullptr;     // [m*L][d] bf16 bits (families with BF16 G)
   uint8_t *d_Gt8 = nullptr;       // [m*L][d] E4M3 codes (families with FP8 G)
-  float *d_gnc = nullptr;         // [m*L][4] column norms per K chunk of the tensor-core path;
-                                  // slots 2, 3: the column's least exponent and its range (int bits)
+  float *d_gnc = nullptr;         // [m*L][kTcColRecord] column norms per K chunk of the tensor-core
+                                  // path; slots 2, 3: the column's least exponent and its range (int
+                                  // bits); slots 4, 5: sum_j |G_j| on that grid (uint64, low word first)
   int32_t *d_Gint = nullptr;      // [m*L][d] column j of G as integers on its own 2^e grid (exact recheck)
   uint32_t *d_status = nullptr;   // sticky status word
   int device = 0;
@@ -173,7 +174,8 @@ cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float
                               cudaStream_t stream);
 
 // Dense E2LSH / SRP on the tensor cores (TMA + tcgen05, BF16 x BF16 -> FP32),
-// for BF16 rows and a family whose G is stored in BF16.  xnc_scratch: [n][4] floats.
+// for BF16 rows and a family whose G is stored in BF16.
+constexpr int kTcColRecord = 8;  // floats per column record of d_gnc
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X);
 int tc_chunk_ktiles(int d, bool fp8);
 size_t tc_dense_scratch_bytes(int64_t n, int64_t ML);

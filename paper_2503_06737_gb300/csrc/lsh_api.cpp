@@ -357,13 +357,13 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
         }
       }
       const int clen = tc_chunk_ktiles(d.d, fp8) * (fp8 ? 128 : 64);
-      std::vector<float> gnc(ml * 4, 0.f);
+      std::vector<float> gnc(ml * kTcColRecord, 0.f);
       std::vector<int32_t> gint(gt.size(), 0);
       for (size_t c = 0; c < ml; ++c) {
         for (int k = 0; k < 2; ++k) {
           double s2 = 0.0;
           for (int j = k * clen; j < std::min(d.d, (k + 1) * clen); ++j) s2 += double(gt[c * d.d + j]) * gt[c * d.d + j];
-          gnc[c * 4 + k] = float(std::sqrt(s2) * (1.0 + 1e-6));
+          gnc[c * kTcColRecord + k] = float(std::sqrt(s2) * (1.0 + 1e-6));
         }
         int emin = 0, emax = 0;
         bool any = false;
@@ -376,14 +376,20 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
           any = true;
         }
         const int range = emax - emin;
+        uint64_t gabs = 0;  // sum of |G_j| on the column's grid (below 2^45: d <= 16384, |G_j| < 2^31)
         if (range <= 23)
           for (int j = 0; j < d.d; ++j) {
             int32_t M;
             int E;
-            if (parts(gt[c * d.d + j], M, E)) gint[c * d.d + j] = M * (int32_t(1) << (E - emin));
+            if (parts(gt[c * d.d + j], M, E)) {
+              gint[c * d.d + j] = M * (int32_t(1) << (E - emin));
+              gabs += uint64_t(gint[c * d.d + j] < 0 ? -int64_t(gint[c * d.d + j]) : int64_t(gint[c * d.d + j]));
+            }
           }
         int32_t slots[2] = {emin, range};
-        std::memcpy(&gnc[c * 4 + 2], slots, sizeof(slots));
+        std::memcpy(&gnc[c * kTcColRecord + 2], slots, sizeof(slots));
+        const uint32_t gw[2] = {uint32_t(gabs), uint32_t(gabs >> 32)};
+        std::memcpy(&gnc[c * kTcColRecord + 4], gw, sizeof(gw));
       }
       if (fp8) e = upload(&f->d_Gt8, g8.data(), g8.size());
       else e = upload(&f->d_Gt16, g16.data(), g16.size());

@@ -34,6 +34,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "internal.h"
@@ -46,7 +47,7 @@ constexpr int BKB = 128;  // bytes of K per tile row: 64 BF16 or 128 E4M3 elemen
 constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps;
 constexpr int CONST_Q = 5;
 constexpr int BW = 8;  // epilogue block: columns read from TMEM at a time  // per-column constants staged per epilogue warp: gn0, gn1, b, ka, kb
-constexpr int XNC_LD = 8, GNC_LD = 4;  // row / column records: NCH chunk norms, exponent base and range
+constexpr int XNC_LD = 8, GNC_LD = kTcColRecord;  // row / column records: NCH chunk norms, exponent base and range
                                        // (rows: then the FP8 row scale)
 static_assert(NCH <= 2, "the chunk norms share a four-word record with the exponent range");
 constexpr int TILE_A = BM * BKB, TILE_B = BN * BKB;
@@ -220,35 +221,46 @@ __device__ __noinline__ double tc_fp64(const TcArgs &a, int64_t row, int64_t col
 }
 
 // The FP64 value of sum_j x_j G[j][c] (ascending j, one rounding per
-// operation) computed by the whole warp exactly, in 64-bit fixed point, in one
-// pass over the row.  A BF16 value is M 2^E with M < 256 an integer; the row
-// (pre-pass) and the column (family set-up) carry their least exponent and
-// exponent range.  With row range Rx <= 23, column range Rg <= 23 and
-// Rx + Rg <= 37, x_j = X_j 2^ex0 and G_jc = G_j 2^eg0 with |X_j|, |G_j| < 2^31
-// and every product X_j G_j below 2^53.  When moreover the sum of the product
-// magnitudes stays below 2^53, every partial sum of the sequential FP64 loop
-// is an integer multiple of 2^(ex0 + eg0) below 2^53 in magnitude, hence exact,
-// so that loop returns the exact sum -- which integer addition (associative)
-// gets in any order.  Returns NaN when a condition fails (the caller then runs
-// the loop); the row is finite, so NaN is no projection value.
-// The exact sum as S 2^e (S below 2^53 in magnitude), in every lane of a
-// group of G consecutive lanes (gl = lane within the group); false when a
-// condition fails.
-template <int G>
-__device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, int64_t col, int gl, long long &S,
-                                                int &e) {
-  const int4 xi = __ldg(reinterpret_cast<const int4 *>(a.xnc + row * XNC_LD));
-  const int4 gi = __ldg(reinterpret_cast<const int4 *>(a.gnc + col * GNC_LD));
-  const int ex0 = xi.z, rx = xi.w, eg0 = gi.z, rg = gi.w;
-  const bool fp8 = a.fp8 != 0;
-  const int per = fp8 ? 16 : 8;  // elements per 16-byte chunk
-  const uint4 *xr = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.X) + row * a.ld * (fp8 ? 1 : 2));
-  const int4 *gr = reinterpret_cast<const int4 *>(a.Gint + col * a.d);
-  // two's complement sum (wraps harmlessly when the magnitude test fails);
-  // the magnitude saturates at 2^53 so that neither a lane nor the reduction overflows
-  unsigned long long sum = 0, mag = 0;
-  constexpr unsigned long long kCap = 1ull << 53;
-  const int nch = a.d / per;
+// operation) computed by a group of G lanes exactly, in 64-bit fixed point.
+// A BF16 value is M 2^E with M < 256 an integer; the row (pre-pass) and the
+// column (family set-up) carry their least exponent and exponent range.  With
+// row range Rx <= 23, column range Rg <= 23 and Rx + Rg <= 37, x_j = X_j 2^ex0
+// and G_jc = G_j 2^eg0 with |X_j|, |G_j| < 2^31 and every product X_j G_j
+// below 2^53.  Every partial sum of the sequential FP64 loop is then an
+// integer multiple of 2^(ex0 + eg0); while each stays below 2^53 in magnitude
+// it is exact, so the loop returns the exact sum -- which integer addition
+// (associative) gets in any order.  The product magnitudes sum to less than
+// 2^(bits of M + Rx) sum_j |G_j| (the column's sum is part of its record):
+// when that is below 2^53 one pass suffices; when it is not (but below 2^62,
+// so that nothing overflows) a second pass takes the partial sums of the
+// ascending loop themselves.  The result is S 2^e (S below 2^53 in magnitude)
+// in every lane of a group of G consecutive lanes (gl = lane within the
+// group); false (the caller runs the FP64 loop) when a condition fails.  The
+// whole warp calls this with the same d (the second pass is warp-uniform).
+//
+// X_j on the row's grid: for BF16 rows whose least exponent keeps 2^-ex0 a
+// normal float, x_j 2^-ex0 is an integer below 2^31 with at most 8
+// significant bits, so one multiply and one conversion give it exactly;
+// otherwise (FP8 rows, rows with subnormal entries) it is assembled from the
+// bit fields.
+template <bool FAST>
+__device__ __forceinline__ int grid_x(const uint32_t (&w)[4], int k, bool fp8, int ex0, float sx) {
+  if (FAST) {
+    const uint32_t h = (k & 1) ? (w[k >> 1] & 0xFFFF0000u) : (w[k >> 1] << 16);
+    return __float2int_rz(__uint_as_float(h) * sx);
+  }
+  int M, E;
+  uint32_t neg;
+  elem_parts(w, k, fp8, M, E, neg);
+  const int X = M << max(E - ex0, 0);  // zero stays zero
+  return neg ? -X : X;
+}
+// First pass: the exact sum (two's complement; it wraps harmlessly when a
+// condition fails).
+template <int G, bool FAST>
+__device__ __forceinline__ long long grid_sum(const uint4 *xr, const int4 *gr, int nch, int per, bool fp8, int ex0,
+                                              float sx, int gl) {
+  long long sum = 0;
 #pragma unroll 2
   for (int c = gl; c < nch; c += G) {
     const uint4 xv = __ldg(xr + c);
@@ -257,28 +269,88 @@ __device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, in
       const int4 g0 = __ldg(gr + (c * per + h) / 4), g1 = __ldg(gr + (c * per + h) / 4 + 1);
       const int gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        int M, E;
-        uint32_t neg;
-        elem_parts(w, h + k, fp8, M, E, neg);
-        const int X = M << max(E - ex0, 0);  // zero stays zero
-        const long long P = (long long)X * gv[k];
-        sum += (unsigned long long)(neg ? -P : P);
-        mag += (unsigned long long)(P < 0 ? -P : P);
+      for (int k = 0; k < 8; ++k) sum += (long long)grid_x<FAST>(w, h + k, fp8, ex0, sx) * gv[k];
+    }
+  }
+  return sum;
+}
+// Second pass: the largest partial sum of the ascending loop in magnitude.
+// The lanes of a group hold consecutive chunks; a chunk's partial sums are its
+// own prefix sums offset by the total of all chunks before it (an exclusive
+// scan over the group plus the running total of the earlier iterations), so
+// their extremes are those of its prefix sums.
+template <int G, bool FAST>
+__device__ __forceinline__ unsigned long long grid_max_partial(const uint4 *xr, const int4 *gr, int nch, int per,
+                                                               bool fp8, int ex0, float sx, int gl, bool active) {
+  long long run = 0;
+  unsigned long long big = 0;
+  for (int c0 = 0; c0 < nch; c0 += G) {
+    const int c = c0 + gl;
+    long long T = 0, qmax = 0, qmin = 0;
+    if (active && c < nch) {
+      const uint4 xv = __ldg(xr + c);
+      const uint32_t w[4] = {xv.x, xv.y, xv.z, xv.w};
+      qmax = LLONG_MIN;
+      qmin = LLONG_MAX;
+      for (int h = 0; h < per; h += 8) {
+        const int4 g0 = __ldg(gr + (c * per + h) / 4), g1 = __ldg(gr + (c * per + h) / 4 + 1);
+        const int gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          T += (long long)grid_x<FAST>(w, h + k, fp8, ex0, sx) * gv[k];
+          qmax = max(qmax, T);
+          qmin = min(qmin, T);
+        }
       }
     }
-    mag = min(mag, kCap);
+    long long incl = T;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, incl, o, G);
+      if (gl >= o) incl += v;
+    }
+    const long long base = run + incl - T;
+    if (active && c < nch) {
+      const long long hi = base + qmax, lo = base + qmin;
+      big = max(big, (unsigned long long)max(hi < 0 ? -hi : hi, lo < 0 ? -lo : lo));
+    }
+    run += __shfl_sync(0xffffffffu, incl, G - 1, G);
   }
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    mag = min(mag + __shfl_xor_sync(0xffffffffu, mag, o), kCap);
-  }
-  S = (long long)sum;
+  for (int o = G / 2; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, o));
+  return big;
+}
+template <int G>
+__device__ __forceinline__ bool exact_sum_group(const TcArgs &a, int64_t row, int64_t col, int gl, long long &S,
+                                                int &e) {
+  const int4 xi = __ldg(reinterpret_cast<const int4 *>(a.xnc + row * XNC_LD));
+  const int4 gi = __ldg(reinterpret_cast<const int4 *>(a.gnc + col * GNC_LD));
+  const uint2 gw = __ldg(reinterpret_cast<const uint2 *>(a.gnc + col * GNC_LD + 4));
+  const unsigned long long gabs = (unsigned long long)gw.y << 32 | gw.x;
+  const int ex0 = xi.z, rx = xi.w, eg0 = gi.z, rg = gi.w;
+  const bool fp8 = a.fp8 != 0;
+  const int per = fp8 ? 16 : 8;  // elements per 16-byte chunk
+  const int nch = a.d / per;
+  const uint4 *xr = reinterpret_cast<const uint4 *>(static_cast<const char *>(a.X) + row * a.ld * (fp8 ? 1 : 2));
+  const int4 *gr = reinterpret_cast<const int4 *>(a.Gint + col * a.d);
+  const bool fast = !fp8 && ex0 >= -127 && ex0 <= 126;
+  const float sx = __int_as_float((127 - ex0) << 23);  // 2^-ex0 (used only when fast)
+  long long sum = fast ? grid_sum<G, true>(xr, gr, nch, per, fp8, ex0, sx, gl)
+                       : grid_sum<G, false>(xr, gr, nch, per, fp8, ex0, sx, gl);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  S = sum;
   e = ex0 + eg0;
-  // every product below 2^53: (M bits) + Rx + (M bits) + Rg <= 53
+  // every product below 2^53: (M bits) + Rx + (M bits) + Rg <= 53; |X_j| < 2^lx
   const int mbits = fp8 ? 4 : 8;
-  return rx <= 23 && rg <= 23 && 2 * mbits + rx + rg <= 53 && mag < kCap;
+  const bool shape = rx <= 23 && rg <= 23 && 2 * mbits + rx + rg <= 53;
+  const int lx = mbits + min(max(rx, 0), 23);  // <= 31
+  const bool one = shape && gabs < (1ull << (53 - lx));
+  const bool second = shape && !one && gabs < (1ull << (62 - lx));
+  if (!__any_sync(0xffffffffu, second)) return one;
+  const unsigned long long big = fast ? grid_max_partial<G, true>(xr, gr, nch, per, fp8, ex0, sx, gl, second)
+                                      : grid_max_partial<G, false>(xr, gr, nch, per, fp8, ex0, sx, gl, second);
+  return one || (second && big < (1ull << 53));
 }
 
 // The oracle's FP64 projection from an exact sum S 2^e: exact, then (FP8 rows)
@@ -918,11 +990,12 @@ int tc_chunk_ktiles(int d, bool fp8) {
   return (ktiles + NCH - 1) / NCH;
 }
 
-// Scratch of one call: the row records [n][4] floats, the queue counter and
-// the recheck queue (16 bytes an entry, about 4x the flag rate seen on
-// Gaussian data; entries beyond it are rechecked inside the main kernel).
+// Scratch of one call: the row records [n][8] floats, the queue counter and
+// the recheck queue (16 bytes an entry, one slot per 256 projections: the
+// flag rate of Gaussian rows at w = 4 grows about as d^2 and is 2.3e-3 at
+// d = 960; entries beyond it are rechecked inside the main kernel, slowly).
 static int64_t tc_queue_cap(int64_t n, int64_t ML) {
-  return std::min<int64_t>(n * ML / 1024 + 65536, int64_t(1) << 28);
+  return std::min<int64_t>(n * ML / 256 + 65536, int64_t(1) << 28);
 }
 static int64_t tc_align16(int64_t b) { return (b + 15) & ~int64_t(15); }
 

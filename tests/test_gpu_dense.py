@@ -97,6 +97,52 @@ def test_dense_bf16_tensor_core_wide_exponents(kind):
     compare_hash(dict(kind=kind, d=256, m=32, L=8, w=4.0, seed=9, compute=1), X)
 
 
+def _grid_regimes(Xb, G):
+    """For every (row, column): which exactness test of the recheck decides it.
+    In units of 2^(least exponent of the row + least exponent of the column),
+    the products are integers; 'one' = the magnitudes sum below 2^52, 'two' =
+    they sum above 2^54 while every partial sum of the ascending loop stays
+    below 2^52 (margins on both sides of 2^53 for the float64 estimates)."""
+    def parts(T):
+        h = T.view(torch.int16).numpy().astype(np.int64) & 0xFFFF
+        e = (h >> 7) & 0xFF
+        return (h & 0x7F) | (np.minimum(e, 1) << 7), np.maximum(e, 1) - 134, np.where(h >> 15, -1, 1)
+    Mx, Ex, sx = parts(Xb)
+    Mg, Eg, sg = parts(G)
+    big = 1 << 20
+    ex0 = np.where(Mx > 0, Ex, big).min(1)
+    eg0 = np.where(Mg > 0, Eg, big).min(0)
+    rx = np.where(Mx > 0, Ex, -big).max(1) - ex0
+    rg = np.where(Mg > 0, Eg, -big).max(0) - eg0
+    Xi = (sx * (Mx << np.maximum(Ex - ex0[:, None], 0))).astype(np.float64)
+    Gi = (sg * (Mg << np.maximum(Eg - eg0[None, :], 0))).astype(np.float64)
+    shape = (rx[:, None] <= 23) & (rg[None, :] <= 23) & (16 + rx[:, None] + rg[None, :] <= 53)
+    mag = np.abs(Xi) @ np.abs(Gi)
+    part = np.stack([np.abs(np.cumsum(Xi[r][:, None] * Gi, axis=0)).max(0) for r in range(Xi.shape[0])])
+    return shape & (mag < 2.0**52), shape & (mag > 2.0**54) & (part < 2.0**52)
+
+
+def test_dense_bf16_tensor_core_recheck_partial_sum_pass():
+    """Rows of +-[1, 2) values with one coordinate near 2^-20: the products'
+    magnitudes sum past 2^53 on the common exponent grid, so the one-pass
+    exactness test fails, while the partial sums of the ascending loop stay
+    below 2^53 -- the recheck's second pass proves them exact.  Bins narrower
+    than the error bound flag every entry, more than the queue holds, so both
+    the recheck kernel and the in-kernel recheck take this route."""
+    import oracle
+    n, d, m, L = 300, 512, 32, 8
+    g = torch.Generator().manual_seed(21)
+    X = (1 + torch.rand(n, d, generator=g)) * (2 * torch.randint(0, 2, (n, d), generator=g) - 1).float()
+    X[torch.arange(n), torch.randint(0, d, (n,), generator=g)] = torch.exp2(-torch.randint(19, 23, (n,), generator=g).float())
+    Xb = X.to(torch.bfloat16)
+    args = dict(kind="e2lsh", d=d, m=m, L=L, w=1e-4, seed=4, compute=1)
+    G = torch.from_numpy(oracle.family("e2lsh", d, m, L, w=1e-4, seed=4, compute=oracle.BF16).G).to(torch.bfloat16)
+    one, two = _grid_regimes(Xb, G)
+    assert two.mean() > 0.2 and one.mean() > 0.1, (two.mean(), one.mean())
+    stats, _ = compare_hash(args, Xb.cuda())
+    assert stats["n_flagged"] >= 0.9 * n * m * L
+
+
 def test_dense_bf16_tensor_core_nonfinite_row():
     X = workloads.iid(300, 128, seed=14, device="cpu", dtype=torch.bfloat16).cuda()
     X[7, 100] = float("inf")
