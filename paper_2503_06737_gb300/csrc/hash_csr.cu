@@ -37,6 +37,7 @@ struct CsrArgs {
   const int32_t *col;
   const float *val;
   const uint16_t *colmajor;   // CS: [d][L] bin | neg << 15
+  uint64_t dmagic[LSH_MAX_MODES];  // HCS: ceil(2^64 / d_k) (0 for d_k = 1), see csr_bin
   int stage_modes;            // HCS per-mode tables staged in shared memory
   int off_acc, off_modes, smem;
   float sqrtm_f, invw_f;
@@ -53,12 +54,17 @@ __device__ __forceinline__ void csr_bin(const CsrArgs &a, int t, int c, const ui
   }
   const uint16_t *hb = mh + int64_t(t) * p.dsum;
   const int8_t *sb = ms + int64_t(t) * p.dsum;
-  int r = c, off = 0, stride = 1;
+  // mode indices i_k of column c (first mode fastest); the quotient by d_k is
+  // the high word of c ceil(2^64 / d_k), exact for every 32-bit c (Lemire,
+  // Kaser and Kurz, "Faster remainder by direct computation", 2019)
+  uint32_t r = uint32_t(c);
+  int off = 0, stride = 1;
   bin = 0;
   neg = 0;
   for (int k = 0; k < p.N; ++k) {
-    const int ik = r % p.dims[k];
-    r /= p.dims[k];
+    const uint32_t q = a.dmagic[k] ? uint32_t(__umul64hi(a.dmagic[k], uint64_t(r))) : r;
+    const int ik = int(r - q * uint32_t(p.dims[k]));
+    r = q;
     bin += int(hb[off + ik]) * stride;
     neg ^= sb[off + ik] < 0 ? 1u : 0u;
     stride *= p.mdims[k];
@@ -271,6 +277,8 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
   a.colmajor = colmajor;
   a.sqrtm_f = float(p.sqrtm);
   a.invw_f = float(1.0 / p.w);
+  for (int k = 0; k < p.N && k < LSH_MAX_MODES; ++k)
+    a.dmagic[k] = p.dims[k] > 1 ? ~0ull / uint64_t(p.dims[k]) + 1 : 0;
   const int acc_bytes = kWarpsPerCta * 2 * p.m * 4;
   a.off_acc = 0;
   a.off_modes = (acc_bytes + 15) & ~15;

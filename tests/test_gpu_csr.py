@@ -2,7 +2,8 @@
 
 Sparse rows are the dense vectors with zeros at unstored positions; the
 oracle's CSR path is itself pinned to its dense path.  Cases: the 20,000-wide
-1%-dense lognormal workload (HCS 100 x 200 -> 16 x 16, m = 256), empty rows,
+1%-dense lognormal workload (HCS 100 x 200 -> 16 x 16, m = 256), HCS with
+odd, unit and power-of-two mode sizes, empty rows,
 single nonzeros, rows longer than a warp, E2LSH on sparse rows, rows with
 unsorted or out-of-range columns (rejected per row), and the full 200,000-row
 workload checked on sampled rows.
@@ -64,6 +65,17 @@ def test_csr_parity(kind, dims, mdims):
     rowptr, cols, vals = _csr_case(600, 20000, 200, seed=3)
     st = _compare(dict(kind=kind, d=20000, m=256, L=5, w=0.5, seed=9, dims=dims, mdims=mdims), rowptr, cols, vals)
     assert st["n_nonfinite"] == 0
+
+
+@pytest.mark.parametrize("kind,dims,mdims", [("hcs_srp", [13, 17, 23], [2, 4, 2]), ("hcs_e2lsh", [1, 71, 71], [1, 4, 4]),
+                                             ("hcs_srp", [2, 2500], [4, 64])])
+def test_csr_hcs_mode_sizes(kind, dims, mdims):
+    """HCS on sparse rows with three odd mode sizes, a mode of size 1, and a
+    power-of-two mode beside a large one: the mode indices of a column come
+    from multiply-high quotients, checked here against the oracle."""
+    rowptr, cols, vals = _csr_case(300, 5000, 60, seed=11)
+    m = int(np.prod(mdims))
+    _compare(dict(kind=kind, d=5000, m=m, L=4, w=0.5, seed=12, dims=dims, mdims=mdims), rowptr, cols, vals)
 
 
 @pytest.mark.parametrize("kind", ["cs_srp", "cs_e2lsh"])
