@@ -224,9 +224,12 @@ void lsh_family_destroy(lsh_family_t fam);
  * CS/HCS call of a shape (device, kind, d, m, L, modes, dtype) with at least
  * 131,072 rows times the candidate tile plans of the hashing kernel on its
  * first 131,072 rows and waits for them (once per shape; skipped while the
- * stream is captured); and calls with stats synchronise.  Temporaries (the
- * recheck queues of batches of 8,192 rows or more and of tensor-core calls)
- * come from the device's stream-ordered memory pool.
+ * stream is captured); and calls with stats synchronise.  Temporaries come
+ * from the device's stream-ordered memory pool: the recheck queue of a
+ * dense-row CS/HCS batch of 8,192 rows or more (16 B per 256 entries of
+ * n*L*m, plus 1 MiB), and for a tensor-core call 32 B of row records per row
+ * plus a queue of 16 B per 256 projections (plus 1 MiB) -- 512 MiB for
+ * 4,000,000 rows with m*L = 2048.
  */
 lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys,
                     float *proj, lsh_hash_stats *stats, void *stream);
