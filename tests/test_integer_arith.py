@@ -1,0 +1,92 @@
+"""The integer arithmetic the kernels rely on, checked on the host.
+
+* Quotients by a mode size d_k as the high word of c * ceil(2^64 / d_k), the
+  constant the host computes per launch for the CSR kernel's HCS mode
+  indices (Lemire, Kaser and Kurz 2019: exact for every 32-bit c when the
+  constant is ceil(2^64 / d) and d < 2^32).
+* The second pass of the tensor-core recheck: the largest partial sum of the
+  ascending loop over the products, assembled from per-chunk prefix-sum
+  extremes offset by an exclusive scan of the chunk totals, the way a group
+  of lanes holding consecutive chunks computes it.  Compared with the direct
+  running sum.
+"""
+import numpy as np
+import pytest
+
+
+def magic(d: int) -> int:
+    """The per-mode constant: (2^64 - 1) // d + 1, 0 for d = 1 (the kernel
+    takes the quotient as c itself then)."""
+    return ((1 << 64) - 1) // d + 1 if d > 1 else 0
+
+
+def quotient(c: int, M: int) -> int:
+    return (M * c) >> 64 if M else c
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 7, 10, 12, 13, 17, 23, 71, 100, 200, 256, 1000, 2500, 4096, 65535, 100003,
+                               (1 << 31) - 1])
+def test_multiply_high_quotient_is_exact(d):
+    M = magic(d)
+    rng = np.random.default_rng(d)
+    cs = [0, 1, d - 1, d, d + 1, 2 * d - 1, (1 << 31) - 1, (1 << 32) - 1]
+    cs += [int(v) for v in rng.integers(0, 1 << 32, size=2000, dtype=np.uint64)]
+    cs += [k * d + r for k in (1, 5, 1000) for r in (0, d - 1) if k * d + r < (1 << 32)]
+    for c in cs:
+        q = quotient(c, M)
+        assert q == c // d, (c, d)
+        assert c - q * d == c % d
+
+
+def test_constant_is_the_ceiling():
+    for d in range(2, 5000):
+        M = magic(d)
+        assert M == -(-(1 << 64) // d)  # ceil(2^64 / d)
+
+
+def max_partial_by_scan(products: np.ndarray, per: int, G: int) -> int:
+    """Largest |partial sum| of the ascending loop, computed the way the kernel
+    does: chunks of `per` products, lane gl of a group of G holding chunk
+    c0 + gl in iteration c0 / G."""
+    n = len(products)
+    nch = n // per
+    run = 0
+    big = 0
+    for c0 in range(0, nch, G):
+        T, qmax, qmin = [0] * G, [0] * G, [0] * G
+        for gl in range(G):
+            c = c0 + gl
+            if c >= nch:
+                continue
+            t, hi, lo = 0, None, None
+            for k in range(per):
+                t += int(products[c * per + k])
+                hi = t if hi is None else max(hi, t)
+                lo = t if lo is None else min(lo, t)
+            T[gl], qmax[gl], qmin[gl] = t, hi, lo
+        incl = np.cumsum(np.array(T, dtype=object))
+        for gl in range(G):
+            if c0 + gl >= nch:
+                continue
+            base = run + int(incl[gl]) - T[gl]
+            big = max(big, abs(base + qmax[gl]), abs(base + qmin[gl]))
+        run += int(incl[G - 1])
+    return big
+
+
+@pytest.mark.parametrize("G,per,d", [(8, 8, 960), (32, 8, 960), (8, 16, 512), (32, 16, 2048), (8, 8, 8), (32, 8, 72)])
+def test_partial_sum_scan_equals_running_sum(G, per, d):
+    rng = np.random.default_rng(G * 1000 + d)
+    for trial in range(20):
+        # integer products of mixed signs and magnitudes (up to 2^52)
+        mag = rng.integers(0, 1 << 20, size=d) << rng.integers(0, 32, size=d)
+        sign = rng.choice([-1, 1], size=d)
+        if trial % 4 == 0:
+            sign[: d // 2] = 1  # a long same-sign run: the extreme is inside a chunk
+        prods = [int(s) * int(m) for s, m in zip(sign, mag)]
+        direct = 0
+        t = 0
+        for p in prods:
+            t += p
+            direct = max(direct, abs(t))
+        assert max_partial_by_scan(np.array(prods, dtype=object), per, G) == direct
