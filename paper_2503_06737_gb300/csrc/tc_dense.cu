@@ -45,10 +45,12 @@ namespace {
 constexpr int BM = 128, BN = 128, KMAX = 8, SB = 5, NCH = 2;
 constexpr int BKB = 128;  // bytes of K per tile row: 64 BF16 or 128 E4M3 elements (one 128-byte swizzle row)
 constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps;
-constexpr int CONST_Q = 5;
-constexpr int BW = 8;  // epilogue block: columns read from TMEM at a time  // per-column constants staged per epilogue warp: gn0, gn1, b, ka, kb
-constexpr int XNC_LD = 8, GNC_LD = kTcColRecord;  // row / column records: NCH chunk norms, exponent base and range
-                                       // (rows: then the FP8 row scale)
+constexpr int CONST_Q = 5;  // per-column constants staged per epilogue warp: gn0, gn1, b, ka, kb
+constexpr int BW = 8;       // epilogue block: columns read from TMEM at a time
+// Row records: NCH chunk norms, least exponent, exponent range, FP8 row scale.
+// Column records: NCH chunk norms, least exponent, exponent range, sum of
+// |G_j| on the column's grid (two words).
+constexpr int XNC_LD = 8, GNC_LD = kTcColRecord;
 static_assert(NCH <= 2, "the chunk norms share a four-word record with the exponent range");
 constexpr int TILE_A = BM * BKB, TILE_B = BN * BKB;
 constexpr uint32_t kSpinLimit = 1u << 26;
