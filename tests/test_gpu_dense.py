@@ -205,3 +205,38 @@ def test_dense_fp8_rows_with_tiny_and_zero_rows():
     X[5] *= 1e-30
     X[7] *= 1e4
     _fp8_compare("e2lsh", 400, 256, 16, 8, seed=5, X=X)
+
+
+@pytest.mark.parametrize("compute", ["bf16", "fp8"])
+def test_dense_tensor_core_full_size_sampled(compute):
+    """4,000,000 x 512 i.i.d. rows, m = 32, L = 64 (GEMM 4M x 512 x 2048): the
+    whole batch is hashed keys-only in one call, as the bench times it (BF16
+    rows, or per-row-scaled FP8 rows); 1,500 sampled rows and the first and
+    last are checked against the oracle bit for bit."""
+    import oracle
+    wl = workloads.WORKLOADS["iid_4M_d512_bf16"]
+    n, d, m, L, w = wl["n"], wl["d"], wl["m"], wl["L"], wl["w"]
+    X = workloads.iid(n, d, seed=1238, device="cuda", dtype=torch.bfloat16)
+    rows = np.concatenate([[0], np.sort(np.random.default_rng(4).choice(np.arange(1, n - 1), 1500, replace=False)),
+                           [n - 1]])
+    rt = torch.as_tensor(rows, device="cuda")
+    if compute == "bf16":
+        fam = lsh.Family("e2lsh", d, m, L, w=w, seed=42, compute=lsh.BF16)
+        out = fam.hash(X, keys=True, stats=True)
+        Xs, dt, rs = X[rt].cpu().view(torch.int16).numpy().view(np.uint16), oracle.BF16, None
+        of = oracle.family("e2lsh", d, m, L, w=w, seed=42, compute=oracle.BF16)
+    else:
+        q8, sc8 = workloads.fp8_rows(X)
+        fam = lsh.Family("e2lsh", d, m, L, w=w, seed=42, compute=lsh.FP8_E4M3)
+        out = fam.hash(q8, keys=True, stats=True, row_scale=sc8)
+        Xs, dt, rs = q8[rt].cpu().numpy(), oracle.E4M3, sc8[rt].cpu().numpy()
+        of = oracle.family("e2lsh", d, m, L, w=w, seed=42, compute=oracle.E4M3)
+        del q8, sc8
+    st, _, _, keys = oracle.hash_dense(of, Xs, dtype=dt, row_scale=rs, want_y=False, want_codes=False)
+    assert st == 0
+    assert np.array_equal(out["keys"][:, rt].cpu().numpy().view(np.uint64), keys)
+    assert out["stats"]["n_entries"] == n * m * L
+    assert out["stats"]["n_changed"] <= out["stats"]["n_flagged"]
+    fam.close()
+    del X, out
+    torch.cuda.empty_cache()

@@ -162,6 +162,31 @@ def test_full_size_gist_like_sampled(kind):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("kind,m,dims,mdims", [("hcs_e2lsh", 16, [8, 16], [4, 4]), ("cs_e2lsh", 12, None, None)])
+def test_full_size_serving_rows_sampled(kind, m, dims, mdims):
+    """10,000,000 x 128 FP16 rows of a 1,024-component mixture, L = 32, w = 48
+    (the serving workload's index): the whole batch hashed keys-only in one
+    call; 1,500 sampled rows and the first and last checked against the oracle."""
+    import oracle
+    wl = workloads.WORKLOADS["gmm1024_10M_d128_f16"]
+    n, d, L = wl["n"], wl["d"], wl["L"]
+    X = workloads.gmm(n, d, wl["components"], seed=1237, device="cuda", dtype=torch.float16)
+    fam = lsh.Family(kind, d, m, L, w=48.0, seed=42, dims=dims, mdims=mdims)
+    out = fam.hash(X, keys=True, stats=True)
+    rows = np.concatenate([[0], np.sort(np.random.default_rng(5).choice(np.arange(1, n - 1), 1500, replace=False)),
+                           [n - 1]])
+    rt = torch.as_tensor(rows, device="cuda")
+    of = oracle.family(kind, d, m, L, w=48.0, seed=42, dims=dims, mdims=mdims)
+    Xs = X[rt].cpu().numpy()
+    st, _, _, keys = oracle.hash_dense(of, Xs, want_y=False, want_codes=False)
+    assert st == 0
+    assert np.array_equal(out["keys"][:, rt].cpu().numpy().view(np.uint64), keys)
+    assert out["stats"]["n_entries"] == n * m * L
+    fam.close()
+    del X, out
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("kind,d,m,L,dims,mdims,dtype", [
     ("cs_e2lsh", 128, 16, 8, None, None, torch.float32),
     ("hcs_e2lsh", 128, 16, 8, [8, 16], [4, 4], torch.bfloat16),
