@@ -32,6 +32,14 @@ MUTANTS = [
      "test_oracle_discretize.py"),
     ("bucket ids not ordered inside a bucket", "return p->id < q->id ? -1 : (p->id > q->id ? 1 : 0);",
      "return p->id > q->id ? -1 : (p->id < q->id ? 1 : 0);", "test_oracle_index.py"),
+    ("key folds swapped (ka and kb)", "return ((uint64_t)a << 32) | (uint64_t)b;",
+     "return ((uint64_t)b << 32) | (uint64_t)a;", "test_oracle_key.py"),
+    ("key fold without the mod 2^32 reduction", "uint32_t a = 0, b = 0;", "uint64_t a = 0, b = 0;",
+     "test_oracle_key.py"),
+    ("codes folded as 16-bit values", "a += (uint32_t)codes[l] * ka[l];",
+     "a += (uint32_t)(uint16_t)codes[l] * ka[l];", "test_oracle_key.py"),
+    ("key multiplier drawn from the low word", "ka[t * m + l] = (uint32_t)(r >> 32) | 1u;",
+     "ka[t * m + l] = (uint32_t)r | 1u;", "test_oracle_key.py"),
 ]
 
 
