@@ -98,7 +98,11 @@ typedef enum {
  *   mdims   HCS sketch sizes per mode, prod = m; CS: {m}.
  *   w       E2LSH bin width (> 0; ignored by SRP kinds, still drawn).
  *   seed    64-bit family seed.
- *   compute element type the dense kinds store G in (LSH_F32 today).
+ *   compute element type the dense kinds store G in: LSH_F32 (the FP32
+ *           draws), LSH_BF16 (each FP32 draw rounded to the nearest BF16,
+ *           ties to even: BF16 rows then run on the tensor cores) or
+ *           LSH_FP8_E4M3 (rounded to E4M3, saturating at 448: per-row-scaled
+ *           FP8 rows run on the tensor cores).  CS/HCS kinds ignore it.
  */
 typedef struct {
   int32_t kind;
@@ -233,6 +237,26 @@ void lsh_family_destroy(lsh_family_t fam);
  */
 lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys,
                     float *proj, lsh_hash_stats *stats, void *stream);
+
+/*
+ * Pin the tile plan of the dense-row CS/HCS hashing kernel for every later
+ * call in this process (any family, any device), in place of the autotuned
+ * one; all five arguments 0 restore the automatic choice.  Every plan
+ * computes the same codes and keys; the plan only sets how the work maps to
+ * the GPU:
+ *   rows_per_lane    1, 2 or 4 rows per thread (one vector shared-memory load
+ *                    per term serves them all);
+ *   row_groups       1, 2 or 4 groups of 32 lanes per row tile, with
+ *                    rows_per_lane * row_groups <= 4;
+ *   warps_per_table  1, 2 or 4 warps sharing the bins of one table;
+ *   tables_per_cta   >= 1, the largest table group a CTA stages (balanced);
+ *   entry_bytes      2 or 4, the width of a member-list entry.
+ * Host only; returns LSH_EINVAL for values outside these sets.  A pinned plan
+ * whose shared memory does not fit a shape (or 2-byte entries for
+ * d * rows_per_lane * 4 > 65535) makes lsh_hash return LSH_EUNSUPPORTED.
+ */
+lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_t warps_per_table,
+                               int32_t tables_per_cta, int32_t entry_bytes);
 
 /*
  * Build the L hash tables of Sec. 3.1 over X: hash (keys only), then per

@@ -2,27 +2,31 @@
 // persistent launch (Definitions 4, 5, 12, 19, 25, 31).
 //
 // Design (sm_103a):
-//   * A CTA owns a group of Lg tables and walks row tiles of 32*RG rows.  Its
-//     tables are staged once in shared memory as per-table member lists: for
-//     each bin, the coordinates j < d with s = +1 (ascending j), then those
-//     with s = -1, each half padded to a multiple of four with the offset of
-//     the row's zero slot, every entry the byte offset 4j (16-bit while
-//     4(d+1) < 2^16, else 32-bit).  HCS lists are derived in the CTA from the
-//     per-mode tables h_k, s_k (the sign of j is prod_k s_k(i_k)), so HBM
-//     holds only O(N d^(1/N)) words per table.
-//   * The row tile is read once from HBM with coalesced loads into a padded
-//     row-major tile (row stride d+1 words: lane r reading row r hits bank
-//     (r + j) mod 32, conflict free; word d is the zero slot).  The next tile
-//     is prefetched into L2 while this one is hashed; the CTAs of the G table
-//     groups that share a tile run concurrently, so it leaves HBM once.
-//   * Lane = row.  A table is split over WPT warps (bins l = k, k+WPT, ...),
-//     which gives the SM enough independent shared-memory loads in flight.
-//     Entries are read four at a time as warp-uniform broadcasts; each x read
-//     is one conflict-free 32-bit load into one of two accumulators per half.
-//     Partial keys of the warps of one table are combined in shared memory:
-//     the key fold is a sum mod 2^32 (E2LSH, SRP m > 64) or an OR of bits
-//     (SRP m <= 64), so partials combine exactly.  The plan (RG, WPT, Lg) is
-//     autotuned per shape on the first large batch (see tuned_plan).
+//   * A CTA owns a group of Lg tables and walks row tiles.  Its tables are
+//     staged once in shared memory as per-table member lists: for each bin,
+//     the coordinates j < d with s = +1 (ascending j), then those with s = -1,
+//     each half padded to a multiple of four with the row's zero slot; every
+//     entry is the byte offset of x_j from a lane's row base (16-bit while it
+//     fits, or 32-bit: one instruction less per term, chosen by the plan).
+//     HCS lists are derived in the CTA from the per-mode tables h_k, s_k (the
+//     sign of j is prod_k s_k(i_k)), so HBM holds only O(N d^(1/N)) words per
+//     table.
+//   * Lane = RPL rows (1, 2 or 4).  The row tile keeps rows in groups of RPL:
+//     inside a group, x_j of its RPL rows are adjacent words, so one
+//     ld.shared.v{1,2,4} fetches the operand of one term for all of a lane's
+//     rows, and one entry (and one address add) serves RPL terms.  Groups are
+//     RPL * dp words apart with dp odd, which keeps the 32 lanes of a warp on
+//     distinct banks.  The tile is read from HBM with 128-bit loads (rows
+//     16-byte aligned) and converted to FP32; the next tile is prefetched into
+//     L2 while this one is hashed, and the CTAs of the G table groups that
+//     share a tile run concurrently, so it leaves HBM once.
+//   * A table is split over WPT warps (bins l = k, k+WPT, ...).  Partial keys
+//     of the warps of one table combine in shared memory: the key fold is a
+//     sum mod 2^32 (E2LSH, SRP m > 64) or an OR of bits (SRP m <= 64).  The
+//     keys-only instantiation carries no per-bin output code; the full one
+//     also writes codes, SRP bits, projections and counters.  The plan (RPL,
+//     row groups, WPT, Lg, entry width) is autotuned per shape on the first
+//     large batch (see tuned_plan).
 //   * Exactness.  The FP32 sum of the k terms of a bin differs from the exact
 //     sum by at most gamma_{k-1} * sum|x_j| <= gamma_{k-1} * k * max|x|
 //     (Higham's bound, any summation order; zero padding adds no error), and
@@ -33,15 +37,16 @@
 //                     <= A max|x| + 10.2u |t| + 15.3u,
 //     using (sqrt(m)|y| + b)/w <= 1.0001 |t| + 2 (b < w), where u = 2^-24 and
 //     A = 1.02 (sqrt(m)/w) gamma_{k-1}(1 + 2 gamma) k; the distance of t to the
-//     nearest integer is computed exactly.  A bin whose t lies within that
-//     bound of an integer (E2LSH), or whose |y| is within A max|x| of 0 (SRP,
-//     A without sqrt(m)/w), gets the canonical value of Definitions 12/19/25/31
-//     -- the ascending FP64 sum, one IEEE rounding per operation: large
-//     batches queue such bins for sketch_recheck_kernel, which patches codes,
-//     bits and keys; small batches (and queue overflow) recheck in place.
-//     Either way the value is computed exactly as an int64 sum on the least
-//     exponent grid of the bin's terms when that sum is exact in the FP64
-//     loop, else by the FP64 loop itself.
+//     nearest integer is computed exactly.  When |t| >= 2^22 the bound is above
+//     2.5 and every such bin is flagged, as is a non-finite t.  A bin whose t
+//     lies within the bound of an integer (E2LSH), or whose |y| is within
+//     A max|x| of 0 (SRP, A without sqrt(m)/w), gets the canonical value of
+//     Definitions 12/19/25/31 -- the ascending FP64 sum, one IEEE rounding per
+//     operation: large batches queue such bins for sketch_recheck_kernel,
+//     which patches codes, bits and keys; small batches (and queue overflow)
+//     recheck in place.  Either way the value is computed exactly as an int64
+//     sum on the least exponent grid of the bin's terms when that sum is exact
+//     in the FP64 loop, else by the FP64 loop itself.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -60,13 +65,14 @@ namespace {
 constexpr int kWarp = 32;
 constexpr float kU32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of FP32
 constexpr int kMaxSmem = 232448;                 // 227 KB opt-in per block
-constexpr int kLoadBatch = 16;                   // row-tile loads in flight per lane
 
 struct Plan {
   int Lg, G, RG, WPT, W, smem;
+  int RPL;       // rows per lane
+  int es;        // entry bytes (2 or 4)
   int cap;       // entry capacity per table (multiple of 4)
+  int dp;        // odd word stride of a row inside a group (>= d + 1)
   int off_ent, off_seg, off_cst, off_key, off_x, off_xmax, off_bad;
-  int x_stride;  // d + 1 words
 };
 
 struct Args {
@@ -74,16 +80,9 @@ struct Args {
   Plan pl;
   int ntiles;
   int slots;     // CTAs per table group
+  int vec;       // rows are 16-byte aligned: 128-bit tile loads
   float sqrtm_f, invw_f;
 };
-
-template <int DT>
-__device__ __forceinline__ float load_x(const void *X, int64_t idx) {
-  if (DT == LSH_F32) return __ldg(reinterpret_cast<const float *>(X) + idx);
-  const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(X) + idx);
-  if (DT == LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
-  return __half2float(__ushort_as_half(h));
-}
 
 // Bin and sign of coordinate j in table t (per-mode tables, first mode fastest).
 __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, int &bin, uint32_t &neg) {
@@ -107,11 +106,11 @@ __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, i
   }
 }
 
-// Stage table t (one warp): member list (sign-split, quad-padded) and the
-// per-bin records seg[l] = {start, quads(+) | quads(-) << 16},
+// Stage table t (one warp): member list (sign-split, quad-padded, entries
+// j * unit) and the per-bin records seg[l] = {start, quads(+) | quads(-) << 16},
 // cst[l] = {b_l (f32 bits), A_l, ka_l, kb_l}.
 template <typename EntT>
-__device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *ent, uint2 *seg,
+__device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_t unit, EntT *ent, uint2 *seg,
                             uint4 *cst, uint32_t *scratch, int lane) {
   const int d = p.d, m = p.m;
   uint32_t *cur = scratch;  // [2m]: counts, then write cursors (key = 2 bin + neg)
@@ -124,7 +123,7 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *e
     atomicAdd(&cur[2 * bin + neg], 1u);
   }
   __syncwarp();
-  const uint32_t zslot = uint32_t(d) << 2;
+  const uint32_t zslot = uint32_t(d) * unit;
   uint32_t carry = 0;
   for (int base = 0; base < m; base += kWarp) {
     const int l = base + lane;
@@ -168,7 +167,7 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *e
       coord_bin(p, t, j, bin, neg);
       const uint32_t key = 2u * uint32_t(bin) + neg;
       const uint32_t peers = __match_any_sync(amask, key);
-      ent[cur[key] + __popc(peers & lt)] = EntT(uint32_t(j) << 2);
+      ent[cur[key] + __popc(peers & lt)] = EntT(uint32_t(j) * unit);
       __syncwarp(amask);
       if ((peers & lt) == 0) cur[key] += __popc(peers);
     }
@@ -176,14 +175,31 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, EntT *e
   }
 }
 
-// Explicit shared-space loads with 32-bit addresses (row tile and entries).
-__device__ __forceinline__ float lds_at(uint32_t saddr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(saddr));
-  return v;
+// Explicit shared-space loads with 32-bit addresses.
+template <int RPL>
+__device__ __forceinline__ void lds_x(uint32_t a, float (&v)[RPL]) {
+  if constexpr (RPL == 1) {
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v[0]) : "r"(a));
+  } else if constexpr (RPL == 2) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
+  } else {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(a));
+  }
 }
-__device__ __forceinline__ void load_quad_s(uint32_t qaddr, bool u16, uint32_t (&o)[4]) {
-  if (u16) {
+template <int RPL>
+__device__ __forceinline__ void sts_x(uint32_t a, const float (&v)[RPL]) {
+  if constexpr (RPL == 1) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v[0]));
+  } else if constexpr (RPL == 2) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v[0]), "f"(v[1]));
+  } else {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
+  }
+}
+template <typename EntT>
+__device__ __forceinline__ void lds_quad(uint32_t qaddr, uint32_t (&o)[4]) {
+  if constexpr (sizeof(EntT) == 2) {
     uint32_t x, y;
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(qaddr));
     o[0] = x & 0xFFFFu;
@@ -200,7 +216,7 @@ __device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off
   return *reinterpret_cast<const float *>(base + off);
 }
 
-// FP64 recheck of one bin for this lane: merge the two ascending halves back
+// FP64 recheck of one bin for one row: merge the two ascending halves back
 // into ascending j and sum s(j) x_j with one IEEE rounding per addition.
 template <typename EntT>
 __device__ __noinline__ double bin_fp64(const EntT *P, int np, const EntT *N, int nn,
@@ -277,12 +293,21 @@ __device__ __noinline__ bool bin_exact(const EntT *P, int np, const EntT *N, int
   return true;
 }
 
+// The exact FP64 projection of one bin of one row of the tile.
+template <typename EntT>
+__device__ __noinline__ double bin_value(const EntT *P, int np4, int nn4, const unsigned char *xr, uint32_t zslot) {
+  double y64;
+  if (!bin_exact(P, np4, P + np4, nn4, xr, y64)) y64 = bin_fp64(P, np4, P + np4, nn4, xr, zslot);
+  return y64;
+}
+
 // Append this lane's flagged bin to the recheck queue (warp-aggregated);
 // false when there is no queue or it is full (the lane then rechecks in place).
 __device__ __forceinline__ bool queue_bin(const SketchLaunch &p, bool flag, int64_t row, int t, int l, int code,
                                           int lane) {
   if (!p.queue) return false;
   const uint32_t bal = __ballot_sync(0xffffffffu, flag);
+  if (!bal) return false;
   const int leader = __ffs(bal) - 1;
   uint32_t base = 0;
   if (lane == leader) base = atomicAdd(p.qcount, uint32_t(__popc(bal)));
@@ -293,21 +318,195 @@ __device__ __forceinline__ bool queue_bin(const SketchLaunch &p, bool flag, int6
   return true;
 }
 
-template <bool SRP, int DT, typename EntT>
-__global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
+// E2LSH code of the exact FP64 projection (Definitions 12, 19; dense:
+// Definition 2 with sqrt(m) = 1), one IEEE rounding per operation; an
+// out-of-range code is INT32_MIN and counted.
+__device__ __forceinline__ int e2lsh_code64(const SketchLaunch &p, double y64, int64_t tl, int &novf) {
+  const double t1 = __dmul_rn(p.sqrtm, y64);
+  const double t2 = __dadd_rn(t1, p.b64[tl]);
+  const double t3 = __ddiv_rn(t2, p.w);
+  const double f = floor(t3);
+  if (f >= -2147483648.0 && f <= 2147483647.0) return int(f);
+  ++novf;
+  return INT32_MIN;
+}
+
+template <int DT>
+__device__ __forceinline__ float load_x(const void *X, int64_t idx) {
+  if (DT == LSH_F32) return __ldg(reinterpret_cast<const float *>(X) + idx);
+  const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(X) + idx);
+  if (DT == LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
+  return __half2float(__ushort_as_half(h));
+}
+
+template <int DT>
+__device__ __forceinline__ float cvt16(uint32_t h) {
+  if (DT == LSH_BF16) return __uint_as_float(h << 16);
+  return __half2float(__ushort_as_half((unsigned short)h));
+}
+
+// 16 bytes of a row (4 FP32 or 8 16-bit values, 16-byte aligned) as FP32.
+template <int DT>
+__device__ __forceinline__ void load_vec(const void *X, int64_t elem, float (&v)[8]) {
+  constexpr int es = DT == LSH_F32 ? 4 : 2;
+  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(static_cast<const char *>(X) + elem * es));
+  if (DT == LSH_F32) {
+    v[0] = __uint_as_float(q.x);
+    v[1] = __uint_as_float(q.y);
+    v[2] = __uint_as_float(q.z);
+    v[3] = __uint_as_float(q.w);
+  } else {
+    v[0] = cvt16<DT>(q.x & 0xFFFFu);
+    v[1] = cvt16<DT>(q.x >> 16);
+    v[2] = cvt16<DT>(q.y & 0xFFFFu);
+    v[3] = cvt16<DT>(q.y >> 16);
+    v[4] = cvt16<DT>(q.z & 0xFFFFu);
+    v[5] = cvt16<DT>(q.z >> 16);
+    v[6] = cvt16<DT>(q.w & 0xFFFFu);
+    v[7] = cvt16<DT>(q.w >> 16);
+  }
+}
+
+// Load the R rows of a tile into the grouped layout (group g at word g*S,
+// row i of the group's x_j at word g*S + j*RPL + i), one warp per group of
+// RPL rows, plus each row's max |x| and finiteness.  With 16-byte aligned
+// rows, lane u reads 16-byte chunk u of each row and writes its V values
+// rotated by rot(lane), which keeps the shared-memory stores of a warp on
+// distinct banks; the remainder (and unaligned rows) go one value at a time.
+template <int DT, int RPL>
+__device__ void load_tile(const Args &a, uint32_t xs_s, int64_t row0, int R, int warp, int lane, float *xmax,
+                          int *bad) {
+  const SketchLaunch &p = a.p;
+  const int d = p.d;
+  const int S = RPL * a.pl.dp;
+  constexpr int V = DT == LSH_F32 ? 4 : 8;
+  const int ngroups = R / RPL;
+  for (int g = warp; g < ngroups; g += a.pl.W) {
+    const uint32_t gb = xs_s + uint32_t(g * S) * 4u;
+    float mx[RPL];
+    bool fin[RPL], live[RPL];
+    int64_t rb[RPL];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      const int64_t row = row0 + g * RPL + i;
+      live[i] = row < p.n;
+      rb[i] = row * p.ld;
+      mx[i] = 0.f;
+      fin[i] = true;
+    }
+    int jdone = 0;
+    if (a.vec) {
+      const int nvec = d / V;
+      const int rot = ((lane * V * RPL) >> 5) & (V - 1);
+      for (int u = lane; u < nvec; u += kWarp) {
+        float v[RPL][8];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          if (live[i]) {
+            load_vec<DT>(p.X, rb[i] + int64_t(u) * V, v[i]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[i][c] = 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < V; ++c) {
+            mx[i] = fmaxf(mx[i], fabsf(v[i][c]));
+            fin[i] = fin[i] && isfinite(v[i][c]);
+          }
+          // rotate left by rot: position c then holds value (c + rot) mod V
+#pragma unroll
+          for (int s = 1; s < V; s <<= 1) {
+            const bool b = (rot & s) != 0;
+            float t[8];
+#pragma unroll
+            for (int c = 0; c < V; ++c) t[c] = b ? v[i][(c + s) & (V - 1)] : v[i][c];
+#pragma unroll
+            for (int c = 0; c < V; ++c) v[i][c] = t[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+          const int j = u * V + ((c + rot) & (V - 1));
+          float o[RPL];
+#pragma unroll
+          for (int i = 0; i < RPL; ++i) o[i] = v[i][c];
+          sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o);
+        }
+      }
+      jdone = nvec * V;
+    }
+    for (int j = jdone + lane; j < d; j += kWarp) {
+      float o[RPL];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        o[i] = live[i] ? load_x<DT>(p.X, rb[i] + j) : 0.f;
+        mx[i] = fmaxf(mx[i], fabsf(o[i]));
+        fin[i] = fin[i] && isfinite(o[i]);
+      }
+      sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o);
+    }
+    if (lane == 0) {  // the zero slot the padding entries point at
+      float z[RPL];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) z[i] = 0.f;
+      sts_x<RPL>(gb + uint32_t(d * RPL) * 4u, z);
+    }
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      float x = mx[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+      const bool allfin = __all_sync(0xffffffffu, fin[i]);
+      if (lane == 0) {
+        xmax[g * RPL + i] = x;
+        bad[g * RPL + i] = allfin ? 0 : 1;
+      }
+    }
+  }
+}
+
+// Sum the terms of nq entry quads into two accumulators per row.
+template <int RPL, typename EntT>
+__device__ __forceinline__ void sum_quads(uint32_t qa, int nq, uint32_t xb, float (&a0)[RPL], float (&a1)[RPL]) {
+#pragma unroll 2
+  for (int q = 0; q < nq; ++q) {
+    uint32_t e[4];
+    lds_quad<EntT>(qa + uint32_t(q) * uint32_t(4 * sizeof(EntT)), e);
+    float v0[RPL], v1[RPL], v2[RPL], v3[RPL];
+    lds_x<RPL>(xb + e[0], v0);
+    lds_x<RPL>(xb + e[1], v1);
+    lds_x<RPL>(xb + e[2], v2);
+    lds_x<RPL>(xb + e[3], v3);
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      a0[i] += v0[i];
+      a1[i] += v1[i];
+      a0[i] += v2[i];
+      a1[i] += v3[i];
+    }
+  }
+}
+
+// Threads per CTA at most: 1024 (64 registers) for one row per lane, 768 for
+// two, 512 for four (their accumulators need more registers).
+constexpr int max_threads(int rpl) { return rpl == 4 ? 512 : (rpl == 2 ? 768 : 1024); }
+
+template <bool SRP, typename EntT, int RPL, bool FULL>
+__global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SketchLaunch &p = a.p;
   const Plan &pl = a.pl;
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = threadIdx.x >> 5;
-  const int g = blockIdx.x % pl.G;
+  const int tg = blockIdx.x % pl.G;
   const int slot = blockIdx.x / pl.G;
-  const int t0 = g * pl.Lg;
+  const int t0 = tg * pl.Lg;
   const int Lg = min(pl.Lg, p.L - t0);
   if (Lg <= 0 || slot >= a.slots) return;
   const int d = p.d, m = p.m;
   const int cap = pl.cap;
   const int WPT = pl.WPT;
+  constexpr uint32_t unit = RPL * 4;
 
   EntT *ent = reinterpret_cast<EntT *>(smem + pl.off_ent);
   uint2 *seg = reinterpret_cast<uint2 *>(smem + pl.off_seg);
@@ -317,58 +516,31 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
   float *xmax = reinterpret_cast<float *>(smem + pl.off_xmax);
   int *bad = reinterpret_cast<int *>(smem + pl.off_bad);
 
-  const float sq_w = a.sqrtm_f * a.invw_f;
   {
+    const float sq_w = a.sqrtm_f * a.invw_f;
     uint32_t *scratch = reinterpret_cast<uint32_t *>(xs) + warp * 2 * m;  // aliases the tile
     for (int tl = warp; tl < Lg; tl += pl.W)
-      stage_table(p, t0 + tl, SRP ? 1.f : sq_w, ent + tl * cap, seg + tl * m, cst + tl * m, scratch, lane);
+      stage_table(p, t0 + tl, SRP ? 1.f : sq_w, unit, ent + tl * cap, seg + tl * m, cst + tl * m, scratch, lane);
   }
   __syncthreads();
 
-  const int R = pl.RG * kWarp;
-  const int xst = pl.x_stride;
+  const int R = pl.RG * kWarp * RPL;
+  const int S = RPL * pl.dp;
   const int ntasks = pl.RG * Lg * WPT;
-  const uint32_t zslot = uint32_t(d) << 2;
-  constexpr int es = DT == LSH_F32 ? 4 : 2;
+  const uint32_t zslot = uint32_t(d) * unit;
+  const uint32_t xs_s = static_cast<uint32_t>(__cvta_generic_to_shared(xs));
+  const uint32_t ent_s = static_cast<uint32_t>(__cvta_generic_to_shared(ent));
+  const int es = p.dtype == LSH_F32 ? 4 : 2;
 
   for (int tile = slot; tile < a.ntiles; tile += a.slots) {
     const int64_t row0 = int64_t(tile) * R;
-    // ---- load the row tile (warp per row, coalesced, kLoadBatch loads in flight) ----
-    for (int r = warp; r < R; r += pl.W) {
-      const int64_t row = row0 + r;
-      float *dst = xs + r * xst;
-      float mx = 0.f;
-      bool fin = true;
-      if (row < p.n) {
-        const int64_t base = row * p.ld;
-        for (int j0 = lane; j0 < d; j0 += kLoadBatch * kWarp) {
-          float v[kLoadBatch];
-#pragma unroll
-          for (int u = 0; u < kLoadBatch; ++u) {
-            const int j = j0 + u * kWarp;
-            v[u] = j < d ? load_x<DT>(p.X, base + j) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < kLoadBatch; ++u) {
-            const int j = j0 + u * kWarp;
-            if (j < d) dst[j] = v[u];
-            mx = fmaxf(mx, fabsf(v[u]));
-            fin = fin && isfinite(v[u]);
-          }
-        }
-      } else {
-        for (int j = lane; j < d; j += kWarp) dst[j] = 0.f;
-      }
-      if (lane == 0) dst[d] = 0.f;  // the zero slot the padding entries point at
-      for (int tl = lane; tl < Lg; tl += kWarp) kacc[r * Lg + tl] = make_uint2(0u, 0u);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const bool allfin = __all_sync(0xffffffffu, fin);
-      if (lane == 0) {
-        xmax[r] = mx;
-        bad[r] = allfin ? 0 : 1;
-      }
-    }
+    for (int i = threadIdx.x; i < R * Lg; i += blockDim.x) kacc[i] = make_uint2(0u, 0u);
+    if (p.dtype == LSH_F32)
+      load_tile<LSH_F32, RPL>(a, xs_s, row0, R, warp, lane, xmax, bad);
+    else if (p.dtype == LSH_BF16)
+      load_tile<LSH_BF16, RPL>(a, xs_s, row0, R, warp, lane, xmax, bad);
+    else
+      load_tile<LSH_F16, RPL>(a, xs_s, row0, R, warp, lane, xmax, bad);
     __syncthreads();
     // ---- prefetch the next tile into L2 while this one is hashed ----
     if (warp == pl.W - 1) {
@@ -383,162 +555,114 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       }
     }
 
-    // ---- one task = (row group, table, bin subset): lane = row ----
+    // ---- one task = (row group, table, bin subset): lane = RPL rows ----
     for (int task = warp; task < ntasks; task += pl.W) {
       const int sub = task % WPT;
       const int rt = task / WPT;
       const int rg = rt / Lg;
       const int tl = rt - rg * Lg;
       const int t = t0 + tl;
-      const int r = rg * kWarp + lane;
-      const int64_t row = row0 + r;
-      const bool valid = row < p.n;
-      const bool isbad = bad[r] != 0;
-      const float xm = xmax[r];
-      const unsigned char *xr = reinterpret_cast<const unsigned char *>(xs + r * xst);
-      const EntT *E = ent + tl * cap;
-      const uint2 *S = seg + tl * m;
+      const int grp = rg * kWarp + lane;  // the lane's row group in the tile
+      const int rl0 = grp * RPL;          // its first row in the tile
+      const uint32_t xb = xs_s + uint32_t(grp * S) * 4u;
+      float xm[RPL];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) xm[i] = xmax[rl0 + i];
+      const uint32_t eb = ent_s + uint32_t(tl * cap) * uint32_t(sizeof(EntT));
+      const uint2 *Sg = seg + tl * m;
       const uint4 *C = cst + tl * m;
-      uint32_t ha = 0, hb = 0;
-      uint64_t word = 0;
+      uint32_t ha[RPL], hb[RPL];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) ha[i] = hb[i] = 0u;
       int nflag = 0, nchanged = 0, novf = 0;
       for (int l = sub; l < m; l += WPT) {
-        const uint2 sg = S[l];
+        const uint2 sg = Sg[l];
         const int qp = int(sg.y & 0xffffu), qn = int(sg.y >> 16);
-        const EntT *Q = E + sg.x;
-        // two quads per iteration (eight loads in flight), then the odd quad;
-        // two accumulators per half (the FP32 error bound holds in any order)
-        constexpr bool kU16 = sizeof(EntT) == 2;
-        constexpr uint32_t kQuadBytes = 4 * sizeof(EntT);
-        const uint32_t xs_a = static_cast<uint32_t>(__cvta_generic_to_shared(xr));
-        uint32_t qa = static_cast<uint32_t>(__cvta_generic_to_shared(Q));
-        float p0 = 0.f, p1 = 0.f;
-        int q = 0;
-#pragma unroll 1
-        for (; q + 2 <= qp; q += 2, qa += 2 * kQuadBytes) {
-          uint32_t e[4], f[4];
-          load_quad_s(qa, kU16, e);
-          load_quad_s(qa + kQuadBytes, kU16, f);
-          p0 += lds_at(xs_a + e[0]);
-          p1 += lds_at(xs_a + e[1]);
-          p0 += lds_at(xs_a + e[2]);
-          p1 += lds_at(xs_a + e[3]);
-          p0 += lds_at(xs_a + f[0]);
-          p1 += lds_at(xs_a + f[1]);
-          p0 += lds_at(xs_a + f[2]);
-          p1 += lds_at(xs_a + f[3]);
-        }
-        if (q < qp) {
-          uint32_t e[4];
-          load_quad_s(qa, kU16, e);
-          qa += kQuadBytes;
-          p0 += lds_at(xs_a + e[0]);
-          p1 += lds_at(xs_a + e[1]);
-          p0 += lds_at(xs_a + e[2]);
-          p1 += lds_at(xs_a + e[3]);
-        }
-        float n0 = 0.f, n1 = 0.f;
-        q = 0;
-#pragma unroll 1
-        for (; q + 2 <= qn; q += 2, qa += 2 * kQuadBytes) {
-          uint32_t e[4], f[4];
-          load_quad_s(qa, kU16, e);
-          load_quad_s(qa + kQuadBytes, kU16, f);
-          n0 += lds_at(xs_a + e[0]);
-          n1 += lds_at(xs_a + e[1]);
-          n0 += lds_at(xs_a + e[2]);
-          n1 += lds_at(xs_a + e[3]);
-          n0 += lds_at(xs_a + f[0]);
-          n1 += lds_at(xs_a + f[1]);
-          n0 += lds_at(xs_a + f[2]);
-          n1 += lds_at(xs_a + f[3]);
-        }
-        if (q < qn) {
-          uint32_t e[4];
-          load_quad_s(qa, kU16, e);
-          n0 += lds_at(xs_a + e[0]);
-          n1 += lds_at(xs_a + e[1]);
-          n0 += lds_at(xs_a + e[2]);
-          n1 += lds_at(xs_a + e[3]);
-        }
-        const float y = (p0 + p1) - (n0 + n1);
+        const uint32_t qa = eb + sg.x * uint32_t(sizeof(EntT));
+        float p0[RPL], p1[RPL], n0[RPL], n1[RPL];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) p0[i] = p1[i] = n0[i] = n1[i] = 0.f;
+        sum_quads<RPL, EntT>(qa, qp, xb, p0, p1);
+        sum_quads<RPL, EntT>(qa + uint32_t(qp) * uint32_t(4 * sizeof(EntT)), qn, xb, n0, n1);
         const uint4 c = C[l];
         const float A = __uint_as_float(c.y);
-        if (SRP) {
-          // A = 0 when the bin holds at most one term: the FP32 value is then exact
-          const bool flag = valid && !isbad && A > 0.f && !(fabsf(y) > A * xm);
-          int bit = y > 0.f ? 1 : 0;
-          if (__any_sync(0xffffffffu, flag)) {
-            if (!queue_bin(p, flag, row, t, l, bit, lane) && flag) {
-              const EntT *P = E + sg.x;
-              double y64;
-              if (!bin_exact(P, 4 * qp, P + 4 * qp, 4 * qn, xr, y64))
-                y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
-              const int b64 = y64 > 0.0 ? 1 : 0;
-              ++nflag;
-              nchanged += b64 != bit;
-              bit = b64;
-            }
-          }
-          if (p.proj && valid) p.proj[(row * p.L + t) * m + l] = y;
-          if (m <= 64) {
-            word |= uint64_t(bit) << l;
-          } else if (bit) {
-            ha += c.z;
-            hb += c.w;
-            if (p.bits && valid)
-              atomicOr(reinterpret_cast<unsigned long long *>(p.bits) + (row * p.L + t) * ((m + 63) >> 6) + (l >> 6),
-                       1ull << (l & 63));
-          }
-        } else {
-          const float bl = __uint_as_float(c.x);
-          const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
-          const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
-          const float M = fmaf(A, xm, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
-          const bool flag = valid && !isbad && !(dist > M && fabsf(tf) < 4194304.f);
-          int code = __float2int_rd(tf);
-          if (__any_sync(0xffffffffu, flag)) {
-            if (!queue_bin(p, flag, row, t, l, code, lane) && flag) {
-              const EntT *P = E + sg.x;
-              double y64;
-              if (!bin_exact(P, 4 * qp, P + 4 * qp, 4 * qn, xr, y64))
-                y64 = bin_fp64(P, 4 * qp, P + 4 * qp, 4 * qn, xr, zslot);
-              const double t1 = __dmul_rn(p.sqrtm, y64);
-              const double t2 = __dadd_rn(t1, p.b64[int64_t(t) * m + l]);
-              const double t3 = __ddiv_rn(t2, p.w);
-              const double f = floor(t3);
-              int c64;
-              if (f >= -2147483648.0 && f <= 2147483647.0) {
-                c64 = int(f);
-              } else {
-                c64 = INT32_MIN;
-                ++novf;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const float y = (p0[i] + p1[i]) - (n0[i] + n1[i]);
+          const int64_t row = row0 + rl0 + i;
+          const unsigned char *xr = reinterpret_cast<const unsigned char *>(xs + grp * S + i);
+          if (SRP) {
+            // A = 0 when the bin holds at most one term: the FP32 value is then exact
+            const bool flag = A > 0.f && !(fabsf(y) > A * xm[i]);
+            int bit = y > 0.f ? 1 : 0;
+            if (__any_sync(0xffffffffu, flag)) {
+              const bool f = flag && row < p.n && !bad[rl0 + i];
+              if (!queue_bin(p, f, row, t, l, bit, lane) && f) {
+                const double y64 = bin_value(ent + tl * cap + sg.x, 4 * qp, 4 * qn, xr, zslot);
+                const int b64 = y64 > 0.0 ? 1 : 0;
+                ++nflag;
+                nchanged += b64 != bit;
+                bit = b64;
               }
-              ++nflag;
-              nchanged += c64 != code;
-              code = c64;
             }
-          }
-          if (isbad) code = INT32_MIN;
-          ha += uint32_t(code) * c.z;
-          hb += uint32_t(code) * c.w;
-          if (valid) {
-            if (p.codes) p.codes[(row * p.L + t) * m + l] = code;
-            if (p.proj) p.proj[(row * p.L + t) * m + l] = y;
+            if (FULL && p.proj && row < p.n) p.proj[(row * p.L + t) * m + l] = y;
+            if (m <= 64) {
+              if (l < 32)
+                ha[i] |= uint32_t(bit) << l;
+              else
+                hb[i] |= uint32_t(bit) << (l - 32);
+            } else if (bit) {
+              ha[i] += c.z;
+              hb[i] += c.w;
+              if (FULL && p.bits && row < p.n)
+                atomicOr(reinterpret_cast<unsigned long long *>(p.bits) + (row * p.L + t) * ((m + 63) >> 6) +
+                             (l >> 6),
+                         1ull << (l & 63));
+            }
+          } else {
+            const float bl = __uint_as_float(c.x);
+            const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
+            const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
+            const float M = fmaf(A, xm[i], fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
+            const bool flag = !(dist > M);
+            int code = __float2int_rd(tf);
+            if (__any_sync(0xffffffffu, flag)) {
+              const bool f = flag && row < p.n && !bad[rl0 + i];
+              if (!queue_bin(p, f, row, t, l, code, lane) && f) {
+                const double y64 = bin_value(ent + tl * cap + sg.x, 4 * qp, 4 * qn, xr, zslot);
+                const int c64 = e2lsh_code64(p, y64, int64_t(t) * m + l, novf);
+                ++nflag;
+                nchanged += c64 != code;
+                code = c64;
+              }
+            }
+            if (FULL) {
+              if (bad[rl0 + i]) code = INT32_MIN;
+              if (row < p.n) {
+                if (p.codes) p.codes[(row * p.L + t) * m + l] = code;
+                if (p.proj) p.proj[(row * p.L + t) * m + l] = y;
+              }
+            }
+            ha[i] += uint32_t(code) * c.z;
+            hb[i] += uint32_t(code) * c.w;
           }
         }
       }
-      // partial key of this warp -> the (row, table) slot
-      if (SRP && m <= 64) {
-        if (word) {
-          atomicOr(&kacc[r * Lg + tl].x, uint32_t(word));
-          atomicOr(&kacc[r * Lg + tl].y, uint32_t(word >> 32));
+      // partial keys of this warp -> the (row, table) slots
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        uint2 *ks = &kacc[(rl0 + i) * Lg + tl];
+        if (WPT == 1) {
+          *ks = make_uint2(ha[i], hb[i]);
+        } else if (SRP && m <= 64) {
+          if (ha[i]) atomicOr(&ks->x, ha[i]);
+          if (hb[i]) atomicOr(&ks->y, hb[i]);
+        } else {
+          atomicAdd(&ks->x, ha[i]);
+          atomicAdd(&ks->y, hb[i]);
         }
-      } else {
-        atomicAdd(&kacc[r * Lg + tl].x, ha);
-        atomicAdd(&kacc[r * Lg + tl].y, hb);
       }
-      if (p.counters) {
+      if (FULL && p.counters) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           nflag += __shfl_xor_sync(0xffffffffu, nflag, o);
@@ -550,9 +674,8 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
           if (nchanged) atomicAdd(p.counters + CNT_CHANGED, (unsigned long long)nchanged);
           if (novf) atomicAdd(p.counters + CNT_OVERFLOW, (unsigned long long)novf);
         }
-      } else if (__any_sync(0xffffffffu, novf != 0) && lane == 0) {
-        atomicOr(p.status, STATUS_OVERFLOW);
       }
+      if (__any_sync(0xffffffffu, novf != 0) && lane == 0) atomicOr(p.status, STATUS_OVERFLOW);
     }
     __syncthreads();
     // ---- keys of the tile: consecutive threads write consecutive rows of a table ----
@@ -564,7 +687,7 @@ __global__ void __launch_bounds__(1024, 1) sketch_dense_kernel(const Args a) {
       uint64_t key;
       if (SRP && m <= 64) {
         key = (uint64_t(k2.y) << 32) | k2.x;
-        if (p.bits) p.bits[row * p.L + t0 + tl] = key;
+        if (FULL && p.bits) p.bits[row * p.L + t0 + tl] = key;
       } else {
         key = (uint64_t(k2.x) << 32) | k2.y;
       }
@@ -594,13 +717,16 @@ int num_sms() {
 
 int align16(int v) { return (v + 15) & ~15; }
 
-// Entry width: 16-bit byte offsets while 4 (d + 1) fits, else 32-bit.
-int entry_bytes(int d) { return 4 * (d + 1) < 65536 ? 2 : 4; }
+// Odd word stride of a row inside a row group (>= d + 1: word d is the zero slot).
+int odd_stride(int d) { return (d + 1) | 1; }
 
-// The shared-memory layout of one plan: RG row groups of 32 rows, WPT warps
-// per table, table groups of (balanced) size <= Lg.  smem > kMaxSmem when it
-// does not fit.
-Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
+// 16-bit entries hold offsets up to the zero slot d * RPL * 4.
+bool entry16_ok(int d, int RPL) { return int64_t(d) * RPL * 4 <= 65535; }
+
+// The shared-memory layout of one plan: RPL rows per lane, RG row groups of
+// 32 lanes, WPT warps per table, table groups of (balanced) size <= Lg,
+// es-byte entries.  smem > kMaxSmem when it does not fit.
+Plan plan_of(int d, int m, int L, int cap, int RPL, int RG, int WPT, int Lg, int es) {
   const int G = (L + Lg - 1) / Lg;
   const int Lgb = (L + G - 1) / G;  // balanced group size
   Plan pl{};
@@ -608,10 +734,13 @@ Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
   pl.G = G;
   pl.RG = RG;
   pl.WPT = WPT;
+  pl.RPL = RPL;
+  pl.es = es;
+  const int maxW = max_threads(RPL) / kWarp;
   const int tasks = RG * Lgb * WPT;
-  int W = tasks < 32 ? tasks : 32;
-  if (tasks > 32) {
-    for (int w = 32; w >= 16; --w)
+  int W = tasks < maxW ? tasks : maxW;
+  if (tasks > maxW) {
+    for (int w = maxW; w >= maxW / 2; --w)
       if (tasks % w == 0) {
         W = w;
         break;
@@ -619,12 +748,12 @@ Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
   }
   if (W < 4) W = 4;
   pl.W = W;
-  pl.x_stride = d + 1;
+  pl.dp = odd_stride(d);
   pl.cap = cap;
-  const int R = RG * kWarp;
+  const int R = RG * kWarp * RPL;
   int off = 0;
   pl.off_ent = off;
-  off = align16(off + Lgb * cap * entry_bytes(d));
+  off = align16(off + Lgb * cap * es);
   pl.off_seg = off;
   off = align16(off + Lgb * m * 8);
   pl.off_cst = off;
@@ -632,9 +761,14 @@ Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
   pl.off_key = off;
   off = align16(off + R * Lgb * 8);
   pl.off_x = off;
-  const int xbytes = R * (d + 1) * 4;
-  const int scratch = W * 2 * m * 4;
-  off = align16(off + (xbytes > scratch ? xbytes : scratch));
+  const int64_t xbytes = int64_t(R) * pl.dp * 4;
+  const int64_t scratch = int64_t(W) * 2 * m * 4;
+  const int64_t big = std::max(xbytes, scratch);
+  if (big > kMaxSmem) {
+    pl.smem = kMaxSmem + 1;
+    return pl;
+  }
+  off = align16(off + int(big));
   pl.off_xmax = off;
   off = align16(off + R * 4);
   pl.off_bad = off;
@@ -643,68 +777,89 @@ Plan plan_of(int d, int m, int L, int cap, int RG, int WPT, int Lg) {
   return pl;
 }
 
-// The default plan: most rows per tile, then two warps per table, then the
-// largest table group that fits.
+// The default plan (no timing): most rows per lane, then most row groups,
+// two warps per table, 16-bit entries where they fit, and the largest table
+// group that fits.  Tiles larger than 32 rows only while every SM gets at
+// least two of them.
 Plan make_plan(int d, int m, int L, int cap, int64_t n) {
   Plan best{};
   best.smem = -1;
   const int sms = num_sms();
-  for (int RG = 4; RG >= 1; RG >>= 1) {
-    const int64_t ntiles = (n + RG * kWarp - 1) / (RG * kWarp);
-    if (RG > 1 && ntiles < 2 * sms) continue;  // keep every SM busy twice over
-    for (int WPT = 2; WPT >= 1; --WPT)
-      for (int Lg = (L < 32 ? L : 32); Lg >= 1; --Lg) {
-        const Plan pl = plan_of(d, m, L, cap, RG, WPT, Lg);
-        if (pl.smem <= kMaxSmem) return pl;
-      }
+  const int shapes[5][2] = {{4, 1}, {2, 1}, {1, 4}, {1, 2}, {1, 1}};
+  for (const auto &sh : shapes) {
+    const int RPL = sh[0], RG = sh[1];
+    const int R = RPL * RG * kWarp;
+    const int64_t ntiles = (n + R - 1) / R;
+    if (R > kWarp && ntiles < 2 * sms) continue;
+    for (int es = entry16_ok(d, RPL) ? 2 : 4; es <= 4; es += 2)
+      for (int WPT = (m >= 2 ? 2 : 1); WPT >= 1; --WPT)
+        for (int Lg = (L < 32 ? L : 32); Lg >= 1; --Lg) {
+          const Plan pl = plan_of(d, m, L, cap, RPL, RG, WPT, Lg, es);
+          if (pl.smem <= kMaxSmem) return pl;
+        }
   }
   return best;
 }
 
-// Candidate plans for the autotuner: for each row-group count and warps per
-// table, the largest fitting table group and the next smaller group count.
+// Candidate plans for the autotuner: for each tile shape, entry width and
+// warps per table, the largest fitting table group and the next smaller
+// group count.
 std::vector<Plan> plan_candidates(int d, int m, int L, int cap, int64_t n) {
   std::vector<Plan> out;
   const int sms = num_sms();
-  for (int RG = 4; RG >= 1; RG >>= 1) {
-    const int64_t ntiles = (n + RG * kWarp - 1) / (RG * kWarp);
-    if (RG > 1 && ntiles < 2 * sms) continue;
-    for (int WPT = 4; WPT >= 1; WPT >>= 1) {
-      if (WPT > m) continue;
-      int found = 0, lastG = -1;
-      for (int Lg = (L < 32 ? L : 32); Lg >= 1 && found < 2; --Lg) {
-        const Plan pl = plan_of(d, m, L, cap, RG, WPT, Lg);
-        if (pl.smem > kMaxSmem || pl.G == lastG) continue;
-        if (pl.RG * pl.Lg * pl.WPT > 1024 / kWarp * 4) continue;
-        lastG = pl.G;
-        out.push_back(pl);
-        ++found;
+  const int shapes[5][2] = {{4, 1}, {2, 1}, {1, 4}, {1, 2}, {1, 1}};
+  for (const auto &sh : shapes) {
+    const int RPL = sh[0], RG = sh[1];
+    const int R = RPL * RG * kWarp;
+    const int64_t ntiles = (n + R - 1) / R;
+    if (R > kWarp && ntiles < 2 * sms) continue;
+    for (int es = entry16_ok(d, RPL) ? 2 : 4; es <= 4; es += 2)
+      for (int WPT = 4; WPT >= 1; WPT >>= 1) {
+        if (WPT > m) continue;
+        int found = 0, lastG = -1;
+        for (int Lg = (L < 32 ? L : 32); Lg >= 1 && found < 2; --Lg) {
+          const Plan pl = plan_of(d, m, L, cap, RPL, RG, WPT, Lg, es);
+          if (pl.smem > kMaxSmem || pl.G == lastG) continue;
+          if (pl.RG * pl.Lg * pl.WPT > 128) continue;
+          lastG = pl.G;
+          out.push_back(pl);
+          ++found;
+        }
       }
-    }
   }
   return out;
 }
 
-template <bool SRP, int DT, typename EntT>
-cudaError_t launch_e(const Args &a, cudaStream_t stream) {
+template <bool SRP, typename EntT, int RPL, bool FULL>
+cudaError_t launch_k(const Args &a, cudaStream_t stream) {
   const dim3 grid((unsigned)(a.slots * a.pl.G)), block((unsigned)(a.pl.W * kWarp));
-  cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<SRP, DT, EntT>,
+  cudaError_t e = cudaFuncSetAttribute(sketch_dense_kernel<SRP, EntT, RPL, FULL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
   if (e != cudaSuccess) return e;
-  sketch_dense_kernel<SRP, DT, EntT><<<grid, block, a.pl.smem, stream>>>(a);
+  sketch_dense_kernel<SRP, EntT, RPL, FULL><<<grid, block, a.pl.smem, stream>>>(a);
   return cudaGetLastError();
 }
 
-template <bool SRP, int DT>
-cudaError_t launch_t(const Args &a, cudaStream_t stream) {
-  return entry_bytes(a.p.d) == 2 ? launch_e<SRP, DT, uint16_t>(a, stream) : launch_e<SRP, DT, uint32_t>(a, stream);
+template <bool SRP, typename EntT, bool FULL>
+cudaError_t launch_r(const Args &a, cudaStream_t stream) {
+  switch (a.pl.RPL) {
+    case 1: return launch_k<SRP, EntT, 1, FULL>(a, stream);
+    case 2: return launch_k<SRP, EntT, 2, FULL>(a, stream);
+    case 4: return launch_k<SRP, EntT, 4, FULL>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool SRP, bool FULL>
+cudaError_t launch_e(const Args &a, cudaStream_t stream) {
+  return a.pl.es == 2 ? launch_r<SRP, uint16_t, FULL>(a, stream) : launch_r<SRP, uint32_t, FULL>(a, stream);
 }
 
 }  // namespace
 
 SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype) {
   (void)dtype;
-  Plan pl = make_plan(d, m, L, cap, int64_t(1) << 40);
+  Plan pl = make_plan(d, m, L, cap, 1);
   SketchPlan sp{};
   sp.ok = pl.smem > 0;
   if (!sp.ok) return sp;
@@ -742,7 +897,7 @@ __global__ void __launch_bounds__(256) sketch_recheck_kernel(const SketchLaunch 
   int nflag = 0, nchanged = 0, novf = 0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x) {
     const int4 r = p.queue[i];
-    const int64_t row = r.x;
+    const int64_t row = int64_t(uint32_t(r.x));
     const int t = r.y, l = r.z;
     const int64_t tl = int64_t(t) * p.m + l;
     const uint32_t start = mseg[2 * tl], np = mseg[2 * tl + 1] & 0xFFFFu, nn = mseg[2 * tl + 1] >> 16;
@@ -798,13 +953,7 @@ __global__ void __launch_bounds__(256) sketch_recheck_kernel(const SketchLaunch 
     if (SRP) {
       c64 = y64 > 0.0 ? 1 : 0;
     } else {
-      const double f = floor(__ddiv_rn(__dadd_rn(__dmul_rn(p.sqrtm, y64), p.b64[tl]), p.w));
-      if (f >= -2147483648.0 && f <= 2147483647.0) {
-        c64 = int(f);
-      } else {
-        c64 = INT32_MIN;
-        ++novf;
-      }
+      c64 = e2lsh_code64(p, y64, tl, novf);
     }
     ++nflag;
     if (c64 == r.w) continue;
@@ -867,10 +1016,11 @@ cudaError_t launch_sketch_recheck(const SketchLaunch &p, const uint16_t *mlist, 
 namespace {
 
 cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stream) {
+  if (p.dtype != LSH_F32 && p.dtype != LSH_BF16 && p.dtype != LSH_F16) return cudaErrorInvalidValue;
   Args a{};
   a.p = p;
   a.pl = pl;
-  const int R = pl.RG * kWarp;
+  const int R = pl.RG * kWarp * pl.RPL;
   const int64_t ntiles = (p.n + R - 1) / R;
   if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
   a.ntiles = int(ntiles);
@@ -878,15 +1028,14 @@ cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stre
   int64_t slots = cap < ntiles ? cap : ntiles;
   if (slots < 1) slots = 1;
   a.slots = int(slots);
+  const int es = p.dtype == LSH_F32 ? 4 : 2;
+  a.vec = (reinterpret_cast<uintptr_t>(p.X) % 16 == 0) && ((p.ld * es) % 16 == 0) ? 1 : 0;
   a.sqrtm_f = float(p.sqrtm);
   a.invw_f = float(1.0 / p.w);
   const bool srp = kind_is_srp(p.kind);
-  switch (p.dtype) {
-    case LSH_F32: return srp ? launch_t<true, LSH_F32>(a, stream) : launch_t<false, LSH_F32>(a, stream);
-    case LSH_BF16: return srp ? launch_t<true, LSH_BF16>(a, stream) : launch_t<false, LSH_BF16>(a, stream);
-    case LSH_F16: return srp ? launch_t<true, LSH_F16>(a, stream) : launch_t<false, LSH_F16>(a, stream);
-    default: return cudaErrorInvalidValue;
-  }
+  const bool full = p.codes || p.bits || p.proj || p.counters;
+  if (srp) return full ? launch_e<true, true>(a, stream) : launch_e<true, false>(a, stream);
+  return full ? launch_e<false, true>(a, stream) : launch_e<false, false>(a, stream);
 }
 
 // Autotuner: the first batch of at least kTuneRows rows of a shape (device,
@@ -894,6 +1043,7 @@ cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stre
 // kTuneRows rows -- keys only, no recheck queue, into the caller's key buffer,
 // which the real launch then overwrites -- and keeps the fastest.  It is
 // skipped while the stream is being captured (the default plan is used).
+// Every plan computes the same codes, and a plan fits any row count.
 constexpr int64_t kTuneRows = 131072;
 
 struct TuneKey {
@@ -960,20 +1110,50 @@ Plan tuned_plan(const SketchLaunch &p, cudaStream_t stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();  // a candidate that failed to launch leaves no sticky error
-  // tuned on kTuneRows rows: keep the row-group choice valid for the real n
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tuned[key] = best;
   return best;
 }
 
+std::mutex g_pin_mu;
+SketchPin g_pin{0, 0, 0, 0, 0};
+
+bool pinned(SketchPin &pin) {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  pin = g_pin;
+  return pin.rows_per_lane != 0;
+}
+
+Plan pinned_plan(const SketchPin &pin, int d, int m, int L, int cap) {
+  if (pin.entry_bytes == 2 && !entry16_ok(d, pin.rows_per_lane)) {
+    Plan bad{};
+    bad.smem = -1;
+    return bad;
+  }
+  return plan_of(d, m, L, cap, pin.rows_per_lane, pin.row_groups, pin.warps_per_table,
+                 std::min(pin.tables_per_cta, L), pin.entry_bytes);
+}
+
 }  // namespace
+
+void set_sketch_pin(const SketchPin &pin) {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin = pin;
+}
+
+bool sketch_pin_fits(int d, int m, int L, int cap) {
+  SketchPin pin;
+  if (!pinned(pin)) return true;
+  const Plan pl = pinned_plan(pin, d, m, L, cap);
+  return pl.smem > 0 && pl.smem <= kMaxSmem;
+}
 
 cudaError_t launch_sketch_dense(const SketchLaunch &p, cudaStream_t stream) {
   if (p.n <= 0) return cudaSuccess;
-  const Plan pl = tuned_plan(p, stream);
+  SketchPin pin;
+  const Plan pl = pinned(pin) ? pinned_plan(pin, p.d, p.m, p.L, p.cap) : tuned_plan(p, stream);
   if (pl.smem <= 0 || pl.smem > kMaxSmem) return cudaErrorInvalidConfiguration;
   return launch_plan(p, pl, stream);
 }
-
 
 }  // namespace lsh

@@ -157,6 +157,11 @@ int64_t sketch_queue_cap(int64_t n, int32_t L, int32_t m);
 // Plan of the dense-row kernel for a shape (for reporting / autotuning).
 struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
 SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
+// Process-wide pinned plan of the dense-row kernel (all zeros: autotuned).
+struct SketchPin { int rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes; };
+void set_sketch_pin(const SketchPin &pin);
+// False when a pinned plan does not fit the shape (the call must not launch).
+bool sketch_pin_fits(int d, int m, int L, int cap);
 
 // CSR-row CS/HCS hashing (all L tables, one launch).  colmajor: count-sketch
 // tables as [d][L] entries bin | neg << 15 (NULL for HCS).

@@ -185,6 +185,8 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   }
   SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, f->sketch_cap, X->dtype);
   if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
+  if (!sketch_pin_fits(d.d, d.m, d.L, f->sketch_cap))
+    return fail(LSH_EUNSUPPORTED, "the pinned sketch plan (lsh_set_sketch_plan) does not fit this shape");
   if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs
     LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
   // large batches (8192 rows or more) defer their boundary rechecks to a
@@ -543,6 +545,22 @@ lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t
     if (stats->n_overflow) return fail(LSH_ERANGE, "E2LSH code outside int32");
   }
   return st;
+}
+
+lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_t warps_per_table,
+                               int32_t tables_per_cta, int32_t entry_bytes) {
+  const bool clear = rows_per_lane == 0 && row_groups == 0 && warps_per_table == 0 && tables_per_cta == 0 &&
+                     entry_bytes == 0;
+  if (!clear) {
+    auto in124 = [](int v) { return v == 1 || v == 2 || v == 4; };
+    if (!in124(rows_per_lane) || !in124(row_groups) || rows_per_lane * row_groups > 4)
+      return fail(LSH_EINVAL, "rows_per_lane and row_groups must be 1, 2 or 4 with a product <= 4");
+    if (!in124(warps_per_table)) return fail(LSH_EINVAL, "warps_per_table must be 1, 2 or 4");
+    if (tables_per_cta < 1) return fail(LSH_EINVAL, "tables_per_cta must be >= 1");
+    if (entry_bytes != 2 && entry_bytes != 4) return fail(LSH_EINVAL, "entry_bytes must be 2 or 4");
+  }
+  set_sketch_pin(SketchPin{rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes});
+  return LSH_OK;
 }
 
 lsh_status lsh_build_index(lsh_family_t fam, const lsh_matrix *X, int32_t keep_data, lsh_index_t *out,

@@ -95,6 +95,7 @@ SIGNATURES = [
     ("lsh_family_status", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     ("lsh_family_destroy", None, [P]),
     ("lsh_hash", ctypes.c_int, [P, ctypes.POINTER(Matrix), P, P, P, ctypes.POINTER(HashStats), P]),
+    ("lsh_set_sketch_plan", ctypes.c_int, [ctypes.c_int32] * 5),
     ("lsh_build_index", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, ctypes.POINTER(P), P]),
     ("lsh_index_rebuild", ctypes.c_int, [P, ctypes.POINTER(Matrix), P]),
     ("lsh_index_rebuild_host", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int64, P]),
@@ -130,6 +131,11 @@ def lib():
 
 def launch_count() -> int:
     return int(lib().lsh_launch_count())
+
+
+def set_sketch_plan(rows_per_lane=0, row_groups=0, warps_per_table=0, tables_per_cta=0, entry_bytes=0):
+    """Pin the dense-row sketch kernel's plan process-wide (all zeros: autotuned)."""
+    _check(lib().lsh_set_sketch_plan(rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes))
 
 
 def _check(st: int):

@@ -68,3 +68,26 @@ def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
         assert rel <= 1e-5, rel
     fam.close()
     return out["stats"], rel
+
+
+def oracle_keys(fam_args: dict, X: torch.Tensor):
+    """Keys [L, n] of the FP64 oracle for the rows of X."""
+    Xh, dt = to_oracle(X)
+    ofam = oracle.family(fam_args["kind"], fam_args["d"], fam_args["m"], fam_args["L"],
+                         w=fam_args.get("w", 4.0), seed=fam_args.get("seed", 42),
+                         dims=fam_args.get("dims"), mdims=fam_args.get("mdims"),
+                         compute=fam_args.get("compute", 0))
+    st, _, _, keys = oracle.hash_dense(ofam, Xh, dtype=dt, want_y=False, want_codes=False)
+    assert st == 0
+    return keys
+
+
+def compare_keys_only(fam_args: dict, X: torch.Tensor):
+    """Hash X for keys only (the lean kernel instantiation) and compare with the oracle."""
+    fam = lsh.Family(**fam_args)
+    out = fam.hash(X, keys=True)
+    torch.cuda.synchronize()
+    gk = out["keys"].cpu().numpy().view(np.uint64)
+    fam.close()
+    keys = oracle_keys(fam_args, X)
+    assert np.array_equal(gk, keys), f"keys differ at {np.argwhere(gk != keys)[:5]}"

@@ -101,3 +101,15 @@ def test_bf16_family_matches_oracle(L, orc, kind):
     g32 = orc.family(kind, 512, 32, 4, seed=77).G
     want = torch.from_numpy(g32).to(torch.bfloat16).to(torch.float32).numpy()
     assert np.array_equal(f.G, want)
+
+
+def test_sketch_plan_pin_validation(L):
+    """The plan pin is host-only: out-of-set values are refused, valid ones and
+    the all-zero reset are accepted (no device needed)."""
+    lib = L.lib()
+    for args in [(3, 1, 1, 1, 2), (4, 2, 1, 1, 2), (1, 1, 3, 1, 2), (1, 1, 1, 0, 2), (1, 1, 1, 4, 3),
+                 (0, 1, 1, 1, 2)]:
+        assert lib.lsh_set_sketch_plan(*args) == 1, args  # LSH_EINVAL
+    for args in [(1, 4, 2, 25, 2), (4, 1, 1, 8, 4), (2, 2, 4, 1, 4)]:
+        assert lib.lsh_set_sketch_plan(*args) == 0, args
+    assert lib.lsh_set_sketch_plan(0, 0, 0, 0, 0) == 0

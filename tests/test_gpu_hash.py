@@ -16,7 +16,7 @@ from paper_2503_06737_gb300 import lsh, workloads
 
 pytestmark = pytest.mark.gpu
 
-from gpu_helpers import compare_hash, to_oracle, unpack_bits  # noqa: E402
+from gpu_helpers import compare_hash, compare_keys_only, to_oracle, unpack_bits  # noqa: E402
 
 
 def _rows(n, d, seed, dtype=torch.float32, kind="iid"):
@@ -232,3 +232,40 @@ def test_deferred_recheck_queue_overflow():
     X = _rows(9000, 128, seed=32)
     stats, _ = compare_hash(dict(kind="cs_e2lsh", d=128, m=16, L=8, w=1e-5, seed=18), X)
     assert stats["n_flagged"] > 0.9 * 9000 * 128
+
+
+# Every plan of the dense-row kernel computes the same codes: pin each shape
+# (rows per lane, row groups, warps per table, tables per CTA, entry bytes)
+# and check the keys-only and the full instantiations against the oracle.
+PLANS = [(1, 1, 1, 4, 2), (1, 1, 2, 50, 4), (1, 2, 4, 8, 2), (1, 4, 1, 3, 4), (2, 1, 2, 6, 2),
+         (2, 1, 1, 16, 4), (2, 2, 1, 5, 2), (4, 1, 2, 4, 2), (4, 1, 4, 2, 4), (4, 1, 1, 32, 2)]
+PLAN_SHAPES = [
+    # kind, d, m, L, dims, mdims, dtype
+    ("cs_e2lsh", 960, 64, 13, None, None, torch.float32),
+    ("hcs_srp", 200, 16, 9, [10, 20], [4, 4], torch.bfloat16),
+    ("cs_srp", 300, 96, 5, None, None, torch.float16),
+    ("hcs_e2lsh", 128, 16, 32, [8, 16], [4, 4], torch.float16),
+]
+
+
+def _pinned(plan, fn):
+    lsh.set_sketch_plan(*plan)
+    try:
+        return fn()
+    except lsh.LshError as e:
+        assert e.status == 6, e  # LSH_EUNSUPPORTED: the pinned plan does not fit this shape
+        return None
+    finally:
+        lsh.set_sketch_plan()
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=[str(p) for p in PLANS])
+@pytest.mark.parametrize("kind,d,m,L,dims,mdims,dtype", PLAN_SHAPES, ids=[s[0] + str(s[1]) for s in PLAN_SHAPES])
+def test_hash_every_plan(plan, kind, d, m, L, dims, mdims, dtype):
+    fa = dict(kind=kind, d=d, m=m, L=L, w=4.0, seed=31, dims=dims, mdims=mdims)
+    X = _rows(1000, d, seed=d + L, dtype=dtype, kind="gmm")
+    _pinned(plan, lambda: compare_hash(fa, X))        # in-place rechecks, codes + proj + stats
+    Xq = _rows(9001, d, seed=d + L + 1, dtype=dtype, kind="gmm")
+    _pinned(plan, lambda: compare_keys_only(fa, Xq))  # queued rechecks, keys only
+    Xu = _rows(301, d + 1, seed=d, dtype=dtype, kind="gmm")[:, 1:]  # rows not 16-byte aligned
+    _pinned(plan, lambda: compare_keys_only(fa, Xu))
