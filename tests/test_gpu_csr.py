@@ -61,10 +61,54 @@ def _compare(args, rowptr, cols, vals, rows=None):
 
 @pytest.mark.parametrize("kind,dims,mdims", [("cs_srp", None, None), ("hcs_srp", [100, 200], [16, 16]),
                                              ("cs_e2lsh", None, None), ("hcs_e2lsh", [100, 200], [16, 16])])
-def test_csr_parity(kind, dims, mdims):
+@pytest.mark.parametrize("L", [5, 8, 20])
+def test_csr_parity(kind, dims, mdims, L):
+    # L a multiple of 4: count-sketch entries (not staged: 20,000 x L x 2 B) come four tables per load
     rowptr, cols, vals = _csr_case(600, 20000, 200, seed=3)
-    st = _compare(dict(kind=kind, d=20000, m=256, L=5, w=0.5, seed=9, dims=dims, mdims=mdims), rowptr, cols, vals)
+    st = _compare(dict(kind=kind, d=20000, m=256, L=L, w=0.5, seed=9, dims=dims, mdims=mdims), rowptr, cols, vals)
     assert st["n_nonfinite"] == 0
+
+
+@pytest.mark.parametrize("kind,d,L", [("cs_srp", 100, 6), ("cs_e2lsh", 3000, 12), ("hcs_srp", 20000, 8)])
+def test_csr_staged_and_long_rows(kind, d, L):
+    """Entries staged in shared memory (small d), rows longer than the 256
+    nonzeros a warp holds in registers (the rest is read per table), and
+    rows of one nonzero."""
+    rng = np.random.default_rng(14)
+    n = 200
+    lens = rng.integers(0, min(d, 700), size=n)
+    lens[:4] = [1, min(d, 257), 0, min(d, 700) - 1]
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    cols = np.concatenate([np.sort(rng.choice(d, size=k, replace=False)) for k in lens]).astype(np.int32)
+    vals = rng.lognormal(size=int(rowptr[-1])).astype(np.float32)
+    dims, mdims = ([100, 200], [4, 8]) if kind.startswith("hcs") else (None, None)
+    _compare(dict(kind=kind, d=d, m=32, L=L, w=0.5, seed=15, dims=dims, mdims=mdims), torch.from_numpy(rowptr),
+             torch.from_numpy(cols), torch.from_numpy(vals))
+
+
+def test_csr_exact_zero_bins():
+    """Bins whose terms cancel exactly (x and -x in one bin), bins of -0.0
+    values only, and all-zero rows: codes and keys still match the oracle."""
+    d, m, L = 64, 8, 4
+    args = dict(kind="cs_srp", d=d, m=m, L=L, seed=3)
+    tabs = lsh.sample_family_tables(**args)
+    h, sg = tabs["bins"][0], tabs["signs"][0]
+    rows, cols, vals = [0], [], []
+    for l in range(m):  # row l: two same-sign members of bin l of table 0 with values v and -v
+        mem = [j for j in range(d) if h[j] == l]
+        same = [j for j in mem if sg[j] == sg[mem[0]]]
+        if len(same) >= 2:
+            cols += [same[0], same[1]]
+            vals += [0.75, -0.75]
+        rows.append(len(cols))
+    cols += [3, 9, 20]
+    vals += [-0.0, -0.0, -0.0]
+    rows.append(len(cols))
+    cols += [1, 2]
+    vals += [0.0, 0.0]
+    rows.append(len(cols))
+    _compare(args, torch.tensor(rows, dtype=torch.int64), torch.tensor(cols, dtype=torch.int32),
+             torch.tensor(vals, dtype=torch.float32))
 
 
 @pytest.mark.parametrize("kind,dims,mdims", [("hcs_srp", [13, 17, 23], [2, 4, 2]), ("hcs_e2lsh", [1, 71, 71], [1, 4, 4]),
@@ -128,3 +172,5 @@ def test_csr_full_size_sampled(kind, dims, mdims):
     assert np.array_equal(out["keys"][:, rt].cpu().numpy().view(np.uint64), keys)
     assert np.array_equal(unpack_bits(out["codes"][rt].cpu().numpy(), wl["m"]), codes)
     assert out["stats"]["n_entries"] == wl["n"] * wl["L"] * wl["m"]
+    ko = fam.hash(csr=(rowptr, cols, vals), keys=True)  # keys only, as the bench times it
+    assert torch.equal(ko["keys"], out["keys"])
