@@ -41,9 +41,17 @@ __global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restric
   __syncthreads();
   const uint64_t *k = keys + int64_t(t) * n;
   const int64_t base = int64_t(tile) * kTile;
-  for (int i = threadIdx.x; i < kTile; i += kThreads) {
-    const int64_t idx = base + i;
-    if (idx < n) atomicAdd(&h[warp][digit_of(k[idx], shift)], 1u);
+  // all kItems loads of a thread in flight before the first use
+  uint64_t kk[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t idx = base + it * kThreads + threadIdx.x;
+    kk[it] = idx < n ? __ldg(k + idx) : 0ull;
+  }
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t idx = base + it * kThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[warp][digit_of(kk[it], shift)], 1u);
   }
   __syncthreads();
   for (int dgt = threadIdx.x; dgt < kRadix; dgt += kThreads) {
@@ -135,12 +143,18 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__rest
   uint32_t rank[kItems];
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t *mycnt = wc + warp * kRadix;
+  // all loads of the tile in flight before the ranking uses them
 #pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const int pos = warp * (kItems * 32) + it * 32 + lane;
     const bool act = pos < count;
-    key[it] = act ? k[base + pos] : ~0ull;
-    id[it] = act ? (ids ? ids[base + pos] : uint32_t(base + pos)) : 0u;
+    key[it] = act ? __ldg(k + base + pos) : ~0ull;
+    id[it] = act ? (ids ? __ldg(ids + base + pos) : uint32_t(base + pos)) : 0u;
+  }
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int pos = warp * (kItems * 32) + it * 32 + lane;
+    const bool act = pos < count;
     const uint32_t dg = act ? digit_of(key[it], shift) : 0xffffffffu;
     const uint32_t peers = __match_any_sync(0xffffffffu, dg);
     uint32_t r = 0;
@@ -256,56 +270,6 @@ __global__ void __launch_bounds__(kThreads) seg_write(const uint64_t *__restrict
 
 }  // namespace
 
-cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out, uint64_t *ukeys_out,
-                         uint32_t *offsets_out, int64_t *nb_out, cudaStream_t stream) {
-  if (L <= 0) return cudaSuccess;
-  if (n == 0) return cudaMemsetAsync(nb_out, 0, sizeof(int64_t) * L, stream);
-  const int ntiles = int((n + kTile - 1) / kTile);
-  const size_t nk = size_t(n) * L;
-  uint64_t *kA = nullptr, *kB = nullptr;
-  uint32_t *iA = nullptr, *hist = nullptr;
-  const size_t hist_len = size_t(kRadix) * ntiles;
-  cudaError_t e;
-  e = cudaMallocAsync(&kA, nk * 8, stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&kB, nk * 8, stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&iA, nk * 4, stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&hist, hist_len * L * 4, stream);
-  const int scatter_smem = kTile * 12 + (kWarps * kRadix + 2 * kRadix + 33) * 4;
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem);
-  // 8 passes, ping-pong so that the last pass writes ids into ids_out:
-  // pass p reads (kin, iin) and writes (kout, iout).
-  const uint64_t *kin = keys;
-  const uint32_t *iin = nullptr;
-  for (int pass = 0; pass < 8 && e == cudaSuccess; ++pass) {
-    uint64_t *kout = (pass % 2 == 0) ? kA : kB;
-    uint32_t *iout = (pass % 2 == 0) ? iA : ids_out;
-    const dim3 grid((unsigned)ntiles, (unsigned)L);
-    radix_hist<<<grid, kThreads, 0, stream>>>(kin, n, pass * 8, ntiles, hist);
-    scan_rows<<<L, 1024, 0, stream>>>(hist, int64_t(hist_len), nullptr);
-    radix_scatter<<<grid, kThreads, scatter_smem, stream>>>(kin, iin, kout, iout, n, pass * 8, ntiles, hist);
-    e = cudaGetLastError();
-    count_launches(3);
-    kin = kout;
-    iin = iout;
-  }
-  // sorted keys in kB, ids in ids_out; buckets
-  if (e == cudaSuccess) {
-    const dim3 grid((unsigned)ntiles, (unsigned)L);
-    uint32_t *bcnt = hist;  // reuse: L * ntiles <= L * hist_len
-    seg_count<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, bcnt);
-    scan_rows<<<L, 1024, 0, stream>>>(bcnt, ntiles, nb_out);
-    seg_write<<<grid, kThreads, 0, stream>>>(kB, n, ntiles, bcnt, nb_out, ukeys_out, offsets_out);
-    e = cudaGetLastError();
-    count_launches(3);
-  }
-  if (kA) cudaFreeAsync(kA, stream);
-  if (kB) cudaFreeAsync(kB, stream);
-  if (iA) cudaFreeAsync(iA, stream);
-  if (hist) cudaFreeAsync(hist, stream);
-  return e;
-}
-
 size_t build_tables_scratch_bytes(int64_t n, int32_t L) {
   if (n <= 0 || L <= 0) return 0;
   const size_t ntiles = size_t((n + kTile - 1) / kTile);
@@ -353,6 +317,19 @@ cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uin
     count_launches(3);
   }
   return e;
+}
+
+// The same build with its scratch from the stream-ordered pool.
+cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out, uint64_t *ukeys_out,
+                         uint32_t *offsets_out, int64_t *nb_out, cudaStream_t stream) {
+  if (L <= 0) return cudaSuccess;
+  if (n == 0) return cudaMemsetAsync(nb_out, 0, sizeof(int64_t) * L, stream);
+  void *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, build_tables_scratch_bytes(n, L), stream);
+  if (e != cudaSuccess) return e;
+  e = build_tables_scratch(keys, n, L, ids_out, ukeys_out, offsets_out, nb_out, scratch, stream);
+  const cudaError_t f = cudaFreeAsync(scratch, stream);
+  return e != cudaSuccess ? e : f;
 }
 
 }  // namespace lsh
