@@ -28,7 +28,10 @@
 // ascending j (the oracle's) as an integer sum on a common 2^e grid, derives
 // the oracle's code from it and patches code, bits and key where the fast
 // code was wrong.  Every mbarrier wait is bounded; a timeout sets an error
-// flag and the kernel still releases its TMEM.
+// flag, and on that path too the producer waits (bounded) for every TMA load
+// it issued and the MMA warp for a final commit of its MMAs, so that no
+// asynchronous copy or MMA is in flight when the CTA releases its TMEM and
+// exits.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   unsigned char *sA = smem;                        // the row tile: KMAX K-slices, resident per row tile
   unsigned char *sB = smem + KMAX * TILE_A;        // G^T K-slices: SB-stage ring
   float4 *consts = reinterpret_cast<float4 *>(smem + KMAX * TILE_A + SB * TILE_B);  // [epi warp][CONST_Q][8]
-  __shared__ __align__(8) uint64_t afull[KMAX], aempty[KMAX], bfull[SB], bempty[SB], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t afull[KMAX], aempty[KMAX], bfull[SB], bempty[SB], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ uint2 kpart[BM][2];  // M = 64: the upper slice's partial keys
   __shared__ volatile int aborted;  // set on a timed-out wait: later waits are skipped
@@ -450,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
     }
+    mbar_init(&mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -467,6 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   if (warp == 0) {
     // producer: the whole warp walks the loop, one elected lane issues
     uint32_t it = 0, mi = 0, s = 0, sph = 0;  // B stage, and the parity of its current fill
+    uint32_t aarm = 0, apar = 0;  // A slots loaded at least once, and the parity of each slot's last load
     bool ok = true;
     for (int64_t mt = blockIdx.x; mt < a.mtiles && ok; mt += gridDim.x, ++mi) {
       const int m0 = int(mt) * BM;
@@ -484,6 +489,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
               break;
             }
             tma_2d_elect(sA + z * TILE_A, &mapA, &afull[z], TILE_A, kt * kBKE, m0);
+            aarm |= 1u << z;
+            apar = (apar & ~(1u << z)) | ((u & 1u) << z);
           }
           if (__any_sync(0xffffffffu, aborted != 0) || (it >= SB && !mbar_wait_warp(&bempty[s], sph ^ 1))) {
             ok = false;
@@ -501,11 +508,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
       atomicOr(a.status, STATUS_TIMEOUT);
       aborted = 1;
     }
-    // let the last loads land before the CTA can exit
-    for (uint32_t k = 0; ok && k < SB && k < it; ++k) {
+    // let every load issued land before the CTA can exit, on the normal and
+    // on the aborted path (bounded waits: a load that never lands ends them)
+    for (uint32_t k = 0; k < SB && k < it; ++k) {
       const uint32_t jj = it - 1 - k;
       if (!mbar_wait_warp(&bfull[jj % SB], (jj / SB) & 1)) break;
     }
+    for (int z = 0; z < KMAX; ++z)
+      if ((aarm >> z) & 1u) mbar_wait_warp(&afull[z], (apar >> z) & 1u);
   } else if (warp == 1) {
     // MMA issue: the whole warp walks the loop, one elected lane issues.
     // Descriptors are precomputed and advanced by adding to their address
@@ -555,8 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
       atomicOr(a.status, STATUS_TIMEOUT);
       aborted = 1;
     }
-    // wait for the last commit so that no MMA is in flight at dealloc
-    if (ok && i > 0) mbar_wait_warp(&tfull[(i - 1) & 1], ((i - 1) >> 1) & 1);
+    // on the normal and on the aborted path: one more commit tracks every MMA
+    // this warp issued; wait for it so that none is in flight at dealloc
+    commit_elect(&mdone);
+    mbar_wait_warp(&mdone, 0);
   } else {
     const int e = warp - 2;
     const int q = warp % 4;
