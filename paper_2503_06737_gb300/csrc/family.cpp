@@ -148,7 +148,10 @@ int sketch_capacity(const HostFamily &hf) {
       ++cnt[size_t(2) * bin + neg];
     }
     int total = 0;
-    for (uint32_t c : cnt) total += int((c + 3) & ~3u);
+    for (int l = 0; l < d.m; ++l) {
+      const uint32_t cp = cnt[size_t(2) * l], cn = cnt[size_t(2) * l + 1];
+      total += cp + cn == 0 ? 4 : int(((cp + 3) & ~3u) + ((cn + 3) & ~3u));  // an empty bin keeps one quad
+    }
     best = std::max(best, total);
   }
   return best;

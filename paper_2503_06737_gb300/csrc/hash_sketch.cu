@@ -72,7 +72,7 @@ struct Plan {
   int es;        // entry bytes (2 or 4)
   int cap;       // entry capacity per table (multiple of 4)
   int dp;        // odd word stride of a row inside a group (>= d + 1)
-  int off_ent, off_seg, off_cst, off_key, off_x, off_xmax, off_bad;
+  int off_ent, off_seg, off_cst, off_rng, off_key, off_x, off_xmax, off_bad, off_ctr;
 };
 
 struct Args {
@@ -83,6 +83,21 @@ struct Args {
   int vec;       // rows are 16-byte aligned: 128-bit tile loads
   float sqrtm_f, invw_f;
 };
+
+// Flag bits in the first entry of every quad of a member list: the quad
+// belongs to the negative half of its bin (kNeg), the quad is the last one of
+// its bin (kEnd).  kMask recovers the offset.
+template <typename EntT>
+struct EntFlags;
+template <>
+struct EntFlags<uint16_t> {
+  static constexpr uint32_t kNeg = 1u << 14, kEnd = 1u << 15, kMask = 0x3fffu;
+};
+template <>
+struct EntFlags<uint32_t> {
+  static constexpr uint32_t kNeg = 1u << 30, kEnd = 1u << 31, kMask = 0x3fffffffu;
+};
+constexpr int kMaxWpt = 4;  // warps per table at most; a table keeps kMaxWpt + 1 range records
 
 // Bin and sign of coordinate j in table t (per-mode tables, first mode fastest).
 __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, int &bin, uint32_t &neg) {
@@ -111,7 +126,7 @@ __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, i
 // cst[l] = {b_l (f32 bits), A_l, ka_l, kb_l}.
 template <typename EntT>
 __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_t unit, EntT *ent, uint2 *seg,
-                            uint4 *cst, uint32_t *scratch, int lane) {
+                            uint4 *cst, uint2 *rng, int wpt, uint32_t *scratch, int lane) {
   const int d = p.d, m = p.m;
   uint32_t *cur = scratch;  // [2m]: counts, then write cursors (key = 2 bin + neg)
   for (int i = lane; i < 2 * m; i += kWarp) cur[i] = 0;
@@ -132,6 +147,7 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
       cp = cur[2 * l];
       cn = cur[2 * l + 1];
       sz = ((cp + 3) & ~3u) + ((cn + 3) & ~3u);
+      if (sz == 0) sz = 4;  // an empty bin keeps one quad of zero slots (it carries the end flag)
     }
     uint32_t s = sz;
 #pragma unroll
@@ -141,7 +157,7 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
     }
     const uint32_t start = carry + s - sz;
     if (l < m) {
-      const uint32_t qp = (cp + 3) & ~3u, qn = (cn + 3) & ~3u;
+      const uint32_t qn = (cn + 3) & ~3u, qp = cp + cn == 0 ? 4u : (cp + 3) & ~3u;
       seg[l] = make_uint2(start, (qp >> 2) | ((qn >> 2) << 16));
       for (uint32_t i = cp; i < qp; ++i) ent[start + i] = EntT(zslot);
       for (uint32_t i = cn; i < qn; ++i) ent[start + qp + i] = EntT(zslot);
@@ -173,6 +189,39 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
     }
     __syncwarp();
   }
+  // flags: negative quads, the last quad of every bin
+  for (int l = lane; l < m; l += kWarp) {
+    const uint2 sg = seg[l];
+    const uint32_t qp = sg.y & 0xffffu, qn = sg.y >> 16;
+    for (uint32_t k = 0; k < qn; ++k) ent[sg.x + 4 * (qp + k)] = EntT(ent[sg.x + 4 * (qp + k)] | EntFlags<EntT>::kNeg);
+    const uint32_t last = sg.x + 4 * (qp + qn - 1);
+    ent[last] = EntT(ent[last] | EntFlags<EntT>::kEnd);
+  }
+  __syncwarp();
+  // the bin ranges of the table's wpt warps, balanced by quads: rng[r] =
+  // {first bin, first quad}, rng[wpt] = {m, total quads}
+  const uint32_t total = (seg[m - 1].x >> 2) + (seg[m - 1].y & 0xffffu) + (seg[m - 1].y >> 16);
+  if (lane <= wpt) {
+    uint32_t lb = 0, qb = 0;
+    if (lane == wpt) {
+      lb = uint32_t(m);
+      qb = total;
+    } else if (lane > 0) {
+      const uint32_t target = (uint32_t(lane) * total) / uint32_t(wpt);
+      uint32_t lo = 0, hi = uint32_t(m);  // first bin whose start quad is >= target
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((seg[mid].x >> 2) < target)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      lb = lo;
+      qb = lo < uint32_t(m) ? (seg[lo].x >> 2) : total;
+    }
+    rng[lane] = make_uint2(lb, qb);
+  }
+  __syncwarp();
 }
 
 // Explicit shared-space loads with 32-bit addresses.
@@ -212,6 +261,26 @@ __device__ __forceinline__ void lds_quad(uint32_t qaddr, uint32_t (&o)[4]) {
   }
 }
 
+// One quad of entries: the four offsets (flags masked off) and the raw
+// first word (whose first entry carries the flags).
+template <typename EntT>
+__device__ __forceinline__ void lds_quad_raw(uint32_t qaddr, uint32_t (&o)[4], uint32_t &w0) {
+  if constexpr (sizeof(EntT) == 2) {
+    uint32_t x, y;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(qaddr));
+    w0 = x;
+    o[0] = x & EntFlags<EntT>::kMask;
+    o[1] = x >> 16;
+    o[2] = y & 0xFFFFu;
+    o[3] = y >> 16;
+  } else {
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3])
+                 : "r"(qaddr));
+    w0 = o[0];
+    o[0] &= EntFlags<EntT>::kMask;
+  }
+}
+
 __device__ __forceinline__ float lds_f32(const unsigned char *base, uint32_t off) {
   return *reinterpret_cast<const float *>(base + off);
 }
@@ -223,9 +292,10 @@ __device__ __noinline__ double bin_fp64(const EntT *P, int np, const EntT *N, in
                                         const unsigned char *xr, uint32_t zslot) {
   int ip = 0, in = 0;
   double y = 0.0;
+  constexpr uint32_t kMask = EntFlags<EntT>::kMask;
   while (true) {
-    const uint32_t a = ip < np ? P[ip] : zslot;
-    const uint32_t b = in < nn ? N[in] : zslot;
+    const uint32_t a = ip < np ? P[ip] & kMask : zslot;
+    const uint32_t b = in < nn ? N[in] & kMask : zslot;
     if (a == zslot && b == zslot) break;
     if (a < b) {
       y = __dadd_rn(y, double(lds_f32(xr, a)));
@@ -258,7 +328,7 @@ __device__ __noinline__ bool bin_exact(const EntT *P, int np, const EntT *N, int
     const EntT *L = h ? N : P;
     const int k = h ? nn : np;
     for (int i = 0; i < k; ++i) {
-      const uint32_t v = __float_as_uint(lds_f32(xr, L[i]));
+      const uint32_t v = __float_as_uint(lds_f32(xr, L[i] & EntFlags<EntT>::kMask));
       if (v & 0x7FFFFFFFu) {
         int E;
         uint32_t M;
@@ -279,7 +349,7 @@ __device__ __noinline__ bool bin_exact(const EntT *P, int np, const EntT *N, int
     const EntT *L = h ? N : P;
     const int k = h ? nn : np;
     for (int i = 0; i < k; ++i) {
-      const uint32_t v = __float_as_uint(lds_f32(xr, L[i]));
+      const uint32_t v = __float_as_uint(lds_f32(xr, L[i] & EntFlags<EntT>::kMask));
       int E;
       uint32_t M;
       fp32_parts(v, E, M);
@@ -331,6 +401,31 @@ __device__ __forceinline__ int e2lsh_code64(const SketchLaunch &p, double y64, i
   return INT32_MIN;
 }
 
+// The rare path of one bin and row (the whole warp calls it when some lane's
+// value lies within the error bound): flagged lanes of valid, finite rows
+// queue the bin, or recheck it in place when there is no queue or it is
+// full.  Returns the lane's code (SRP: bit) and, in ev, bit 0 = rechecked in
+// place, bit 1 = its code changed, bit 2 = the code overflowed int32.
+struct ColdOut {
+  int code, ev;
+};
+template <bool SRP, typename EntT>
+__device__ __noinline__ ColdOut bin_cold(const SketchLaunch &p, bool flag, int64_t row, int t, int l, int code,
+                                         const EntT *P, int qp, int qn, const unsigned char *xr, uint32_t zslot,
+                                         int lane) {
+  ColdOut o{code, 0};
+  if (queue_bin(p, flag, row, t, l, code, lane) || !flag) return o;
+  const double y64 = bin_value(P, 4 * qp, 4 * qn, xr, zslot);
+  int c64, novf = 0;
+  if (SRP)
+    c64 = y64 > 0.0 ? 1 : 0;
+  else
+    c64 = e2lsh_code64(p, y64, int64_t(t) * p.m + l, novf);
+  o.ev = 1 | (c64 != code ? 2 : 0) | (novf ? 4 : 0);
+  o.code = c64;
+  return o;
+}
+
 template <int DT>
 __device__ __forceinline__ float load_x(const void *X, int64_t idx) {
   if (DT == LSH_F32) return __ldg(reinterpret_cast<const float *>(X) + idx);
@@ -345,11 +440,9 @@ __device__ __forceinline__ float cvt16(uint32_t h) {
   return __half2float(__ushort_as_half((unsigned short)h));
 }
 
-// 16 bytes of a row (4 FP32 or 8 16-bit values, 16-byte aligned) as FP32.
+// 16 bytes of a row (4 FP32 or 8 16-bit values) as FP32.
 template <int DT>
-__device__ __forceinline__ void load_vec(const void *X, int64_t elem, float (&v)[8]) {
-  constexpr int es = DT == LSH_F32 ? 4 : 2;
-  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(static_cast<const char *>(X) + elem * es));
+__device__ __forceinline__ void unpack_vec(const uint4 q, float (&v)[8]) {
   if (DT == LSH_F32) {
     v[0] = __uint_as_float(q.x);
     v[1] = __uint_as_float(q.y);
@@ -396,54 +489,80 @@ __device__ void load_tile(const Args &a, uint32_t xs_s, int64_t row0, int R, int
     }
     int jdone = 0;
     if (a.vec) {
+      // NB chunks per lane in flight: all loads of a batch issue before use
+      constexpr int NB = 8 / RPL;
       const int nvec = d / V;
       const int rot = ((lane * V * RPL) >> 5) & (V - 1);
-      for (int u = lane; u < nvec; u += kWarp) {
-        float v[RPL][8];
+      for (int u0 = lane; u0 < nvec; u0 += NB * kWarp) {
+        uint4 q[NB][RPL];
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          if (live[i]) {
-            load_vec<DT>(p.X, rb[i] + int64_t(u) * V, v[i]);
-          } else {
+        for (int b = 0; b < NB; ++b) {
+          const int u = u0 + b * kWarp;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[i][c] = 0.f;
-          }
-#pragma unroll
-          for (int c = 0; c < V; ++c) {
-            mx[i] = fmaxf(mx[i], fabsf(v[i][c]));
-            fin[i] = fin[i] && isfinite(v[i][c]);
-          }
-          // rotate left by rot: position c then holds value (c + rot) mod V
-#pragma unroll
-          for (int s = 1; s < V; s <<= 1) {
-            const bool b = (rot & s) != 0;
-            float t[8];
-#pragma unroll
-            for (int c = 0; c < V; ++c) t[c] = b ? v[i][(c + s) & (V - 1)] : v[i][c];
-#pragma unroll
-            for (int c = 0; c < V; ++c) v[i][c] = t[c];
+          for (int i = 0; i < RPL; ++i) {
+            constexpr int es = DT == LSH_F32 ? 4 : 2;
+            q[b][i] = (u < nvec && live[i])
+                          ? __ldg(reinterpret_cast<const uint4 *>(static_cast<const char *>(p.X) +
+                                                                  (rb[i] + int64_t(u) * V) * es))
+                          : make_uint4(0u, 0u, 0u, 0u);
           }
         }
 #pragma unroll
-        for (int c = 0; c < V; ++c) {
-          const int j = u * V + ((c + rot) & (V - 1));
-          float o[RPL];
+        for (int b = 0; b < NB; ++b) {
+          const int u = u0 + b * kWarp;
+          if (u >= nvec) break;
+          float v[RPL][8];
 #pragma unroll
-          for (int i = 0; i < RPL; ++i) o[i] = v[i][c];
-          sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o);
+          for (int i = 0; i < RPL; ++i) {
+            unpack_vec<DT>(q[b][i], v[i]);
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+              mx[i] = fmaxf(mx[i], fabsf(v[i][c]));
+              fin[i] = fin[i] && isfinite(v[i][c]);
+            }
+            // rotate left by rot: position c then holds value (c + rot) mod V
+#pragma unroll
+            for (int sft = 1; sft < V; sft <<= 1) {
+              const bool bsel = (rot & sft) != 0;
+              float t[8];
+#pragma unroll
+              for (int c = 0; c < V; ++c) t[c] = bsel ? v[i][(c + sft) & (V - 1)] : v[i][c];
+#pragma unroll
+              for (int c = 0; c < V; ++c) v[i][c] = t[c];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < V; ++c) {
+            const int j = u * V + ((c + rot) & (V - 1));
+            float o[RPL];
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) o[i] = v[i][c];
+            sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o);
+          }
         }
       }
       jdone = nvec * V;
     }
-    for (int j = jdone + lane; j < d; j += kWarp) {
-      float o[RPL];
+    // the remainder (and unaligned rows): 8 values per lane in flight
+    for (int j0 = jdone + lane; j0 < d; j0 += 8 * kWarp) {
+      float o[8][RPL];
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        o[i] = live[i] ? load_x<DT>(p.X, rb[i] + j) : 0.f;
-        mx[i] = fmaxf(mx[i], fabsf(o[i]));
-        fin[i] = fin[i] && isfinite(o[i]);
+      for (int b = 0; b < 8; ++b) {
+        const int j = j0 + b * kWarp;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) o[b][i] = (j < d && live[i]) ? load_x<DT>(p.X, rb[i] + j) : 0.f;
       }
-      sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int j = j0 + b * kWarp;
+        if (j >= d) break;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          mx[i] = fmaxf(mx[i], fabsf(o[b][i]));
+          fin[i] = fin[i] && isfinite(o[b][i]);
+        }
+        sts_x<RPL>(gb + uint32_t(j * RPL) * 4u, o[b]);
+      }
     }
     if (lane == 0) {  // the zero slot the padding entries point at
       float z[RPL];
@@ -487,12 +606,19 @@ __device__ __forceinline__ void sum_quads(uint32_t qa, int nq, uint32_t xb, floa
   }
 }
 
-// Threads per CTA at most: 1024 (64 registers) for one row per lane, 768 for
-// two, 512 for four (their accumulators need more registers).
-constexpr int max_threads(int rpl) { return rpl == 4 ? 512 : (rpl == 2 ? 768 : 1024); }
+// The next task of the tile for this warp (lane 0 takes it from the counter).
+__device__ __forceinline__ int claim_task(uint32_t *ctr, int lane) {
+  uint32_t t = 0;
+  if (lane == 0) t = atomicAdd(ctr, 1u);
+  return int(__shfl_sync(0xffffffffu, t, 0));
+}
+
+// Threads per CTA at most: 768 (80 registers) for one or two rows per lane,
+// 512 for four (their accumulators need more registers).
+constexpr int max_threads(int rpl) { return rpl == 4 ? 512 : 768; }
 
 template <bool SRP, typename EntT, int RPL, bool FULL>
-__global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const Args a) {
+__global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SketchLaunch &p = a.p;
   const Plan &pl = a.pl;
@@ -510,18 +636,22 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
 
   EntT *ent = reinterpret_cast<EntT *>(smem + pl.off_ent);
   uint2 *seg = reinterpret_cast<uint2 *>(smem + pl.off_seg);
+  uint2 *rng = reinterpret_cast<uint2 *>(smem + pl.off_rng);  // [Lg][kMaxWpt + 1] warp ranges
   uint4 *cst = reinterpret_cast<uint4 *>(smem + pl.off_cst);
   uint2 *kacc = reinterpret_cast<uint2 *>(smem + pl.off_key);  // [R][Lg] partial keys
   float *xs = reinterpret_cast<float *>(smem + pl.off_x);
   float *xmax = reinterpret_cast<float *>(smem + pl.off_xmax);
   int *bad = reinterpret_cast<int *>(smem + pl.off_bad);
+  uint32_t *task_ctr = reinterpret_cast<uint32_t *>(smem + pl.off_ctr);
 
   {
     const float sq_w = a.sqrtm_f * a.invw_f;
     uint32_t *scratch = reinterpret_cast<uint32_t *>(xs) + warp * 2 * m;  // aliases the tile
     for (int tl = warp; tl < Lg; tl += pl.W)
-      stage_table(p, t0 + tl, SRP ? 1.f : sq_w, unit, ent + tl * cap, seg + tl * m, cst + tl * m, scratch, lane);
+      stage_table(p, t0 + tl, SRP ? 1.f : sq_w, unit, ent + tl * cap, seg + tl * m, cst + tl * m,
+                  rng + tl * (kMaxWpt + 1), WPT, scratch, lane);
   }
+  if (threadIdx.x == 0) *task_ctr = 0u;
   __syncthreads();
 
   const int R = pl.RG * kWarp * RPL;
@@ -555,8 +685,10 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
       }
     }
 
-    // ---- one task = (row group, table, bin subset): lane = RPL rows ----
-    for (int task = warp; task < ntasks; task += pl.W) {
+    // ---- one task = (row group, table, bin range): lane = RPL rows.  Warps
+    // claim tasks from a shared counter, so the ones that finish early take
+    // more and the barrier at the end of the tile waits for one task at most ----
+    for (int task = claim_task(task_ctr, lane); task < ntasks; task = claim_task(task_ctr, lane)) {
       const int sub = task % WPT;
       const int rt = task / WPT;
       const int rg = rt / Lg;
@@ -575,43 +707,52 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
 #pragma unroll
       for (int i = 0; i < RPL; ++i) ha[i] = hb[i] = 0u;
       int nflag = 0, nchanged = 0, novf = 0;
-      for (int l = sub; l < m; l += WPT) {
-        const uint2 sg = Sg[l];
-        const int qp = int(sg.y & 0xffffu), qn = int(sg.y >> 16);
-        const uint32_t qa = eb + sg.x * uint32_t(sizeof(EntT));
-        float p0[RPL], p1[RPL], n0[RPL], n1[RPL];
+      // this warp's bins: a contiguous range, walked as one flat list of
+      // quads; the last quad of every bin ends in that bin's epilogue
+      const uint2 rb = rng[tl * (kMaxWpt + 1) + sub], rn = rng[tl * (kMaxWpt + 1) + sub + 1];
+      int l = int(rb.x);
+      float a0[RPL], a1[RPL];
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) p0[i] = p1[i] = n0[i] = n1[i] = 0.f;
-        sum_quads<RPL, EntT>(qa, qp, xb, p0, p1);
-        sum_quads<RPL, EntT>(qa + uint32_t(qp) * uint32_t(4 * sizeof(EntT)), qn, xb, n0, n1);
+      for (int i = 0; i < RPL; ++i) a0[i] = a1[i] = 0.f;
+      auto finish_bin = [&]() {
         const uint4 c = C[l];
         const float A = __uint_as_float(c.y);
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
-          const float y = (p0[i] + p1[i]) - (n0[i] + n1[i]);
+          const float y = a0[i] + a1[i];
+          a0[i] = a1[i] = 0.f;
           const int64_t row = row0 + rl0 + i;
-          const unsigned char *xr = reinterpret_cast<const unsigned char *>(xs + grp * S + i);
+          int code;
+          bool flag;
           if (SRP) {
             // A = 0 when the bin holds at most one term: the FP32 value is then exact
-            const bool flag = A > 0.f && !(fabsf(y) > A * xm[i]);
-            int bit = y > 0.f ? 1 : 0;
-            if (__any_sync(0xffffffffu, flag)) {
-              const bool f = flag && row < p.n && !bad[rl0 + i];
-              if (!queue_bin(p, f, row, t, l, bit, lane) && f) {
-                const double y64 = bin_value(ent + tl * cap + sg.x, 4 * qp, 4 * qn, xr, zslot);
-                const int b64 = y64 > 0.0 ? 1 : 0;
-                ++nflag;
-                nchanged += b64 != bit;
-                bit = b64;
-              }
-            }
+            flag = A > 0.f && !(fabsf(y) > A * xm[i]);
+            code = y > 0.f ? 1 : 0;
+          } else {
+            const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, __uint_as_float(c.x)), a.invw_f);
+            const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
+            const float M = fmaf(A, xm[i], fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
+            flag = !(dist > M);
+            code = __float2int_rd(tf);
+          }
+          if (__any_sync(0xffffffffu, flag)) {
+            const uint2 sg = Sg[l];
+            const ColdOut o = bin_cold<SRP>(p, flag && row < p.n && !bad[rl0 + i], row, t, l, code,
+                                            ent + tl * cap + sg.x, int(sg.y & 0xffffu), int(sg.y >> 16),
+                                            reinterpret_cast<const unsigned char *>(xs + grp * S + i), zslot, lane);
+            code = o.code;
+            nflag += o.ev & 1;
+            nchanged += (o.ev >> 1) & 1;
+            novf += (o.ev >> 2) & 1;
+          }
+          if (SRP) {
             if (FULL && p.proj && row < p.n) p.proj[(row * p.L + t) * m + l] = y;
             if (m <= 64) {
               if (l < 32)
-                ha[i] |= uint32_t(bit) << l;
+                ha[i] |= uint32_t(code) << l;
               else
-                hb[i] |= uint32_t(bit) << (l - 32);
-            } else if (bit) {
+                hb[i] |= uint32_t(code) << (l - 32);
+            } else if (code) {
               ha[i] += c.z;
               hb[i] += c.w;
               if (FULL && p.bits && row < p.n)
@@ -620,22 +761,6 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
                          1ull << (l & 63));
             }
           } else {
-            const float bl = __uint_as_float(c.x);
-            const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
-            const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
-            const float M = fmaf(A, xm[i], fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
-            const bool flag = !(dist > M);
-            int code = __float2int_rd(tf);
-            if (__any_sync(0xffffffffu, flag)) {
-              const bool f = flag && row < p.n && !bad[rl0 + i];
-              if (!queue_bin(p, f, row, t, l, code, lane) && f) {
-                const double y64 = bin_value(ent + tl * cap + sg.x, 4 * qp, 4 * qn, xr, zslot);
-                const int c64 = e2lsh_code64(p, y64, int64_t(t) * m + l, novf);
-                ++nflag;
-                nchanged += c64 != code;
-                code = c64;
-              }
-            }
             if (FULL) {
               if (bad[rl0 + i]) code = INT32_MIN;
               if (row < p.n) {
@@ -647,7 +772,29 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
             hb[i] += uint32_t(code) * c.w;
           }
         }
-      }
+        ++l;
+      };
+      auto step = [&](uint32_t q) {
+        uint32_t e[4], w0;
+        lds_quad_raw<EntT>(eb + q * uint32_t(4 * sizeof(EntT)), e, w0);
+        const float sgn = (w0 & EntFlags<EntT>::kNeg) ? -1.f : 1.f;
+        float v0[RPL], v1[RPL], v2[RPL], v3[RPL];
+        lds_x<RPL>(xb + e[0], v0);
+        lds_x<RPL>(xb + e[1], v1);
+        lds_x<RPL>(xb + e[2], v2);
+        lds_x<RPL>(xb + e[3], v3);
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {  // x * (+-1) is exact: each fma is one rounded addition
+          a0[i] = __fmaf_rn(v0[i], sgn, a0[i]);
+          a1[i] = __fmaf_rn(v1[i], sgn, a1[i]);
+          a0[i] = __fmaf_rn(v2[i], sgn, a0[i]);
+          a1[i] = __fmaf_rn(v3[i], sgn, a1[i]);
+        }
+        if (w0 & EntFlags<EntT>::kEnd) finish_bin();
+      };
+      const uint32_t qend = rn.y;
+#pragma unroll 1
+      for (uint32_t q = rb.y; q < qend; ++q) step(q);
       // partial keys of this warp -> the (row, table) slots
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
@@ -679,6 +826,7 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
     }
     __syncthreads();
     // ---- keys of the tile: consecutive threads write consecutive rows of a table ----
+    if (threadIdx.x == 0) *task_ctr = 0u;  // claimed again after the next tile's load barrier
     for (int i = threadIdx.x; i < Lg * R; i += blockDim.x) {
       const int tl = i / R, r = i - tl * R;
       const int64_t row = row0 + r;
@@ -720,8 +868,9 @@ int align16(int v) { return (v + 15) & ~15; }
 // Odd word stride of a row inside a row group (>= d + 1: word d is the zero slot).
 int odd_stride(int d) { return (d + 1) | 1; }
 
-// 16-bit entries hold offsets up to the zero slot d * RPL * 4.
-bool entry16_ok(int d, int RPL) { return int64_t(d) * RPL * 4 <= 65535; }
+// 16-bit entries hold offsets up to the zero slot d * RPL * 4 in 14 bits
+// (bits 14 and 15 of a quad's first entry are its flags).
+bool entry16_ok(int d, int RPL) { return int64_t(d) * RPL * 4 <= 0x3fff; }
 
 // The shared-memory layout of one plan: RPL rows per lane, RG row groups of
 // 32 lanes, WPT warps per table, table groups of (balanced) size <= Lg,
@@ -758,6 +907,8 @@ Plan plan_of(int d, int m, int L, int cap, int RPL, int RG, int WPT, int Lg, int
   off = align16(off + Lgb * m * 8);
   pl.off_cst = off;
   off = align16(off + Lgb * m * 16);
+  pl.off_rng = off;
+  off = align16(off + Lgb * (kMaxWpt + 1) * 8);
   pl.off_key = off;
   off = align16(off + R * Lgb * 8);
   pl.off_x = off;
@@ -773,6 +924,8 @@ Plan plan_of(int d, int m, int L, int cap, int RPL, int RG, int WPT, int Lg, int
   off = align16(off + R * 4);
   pl.off_bad = off;
   off = align16(off + R * 4);
+  pl.off_ctr = off;
+  off = align16(off + 4);
   pl.smem = off;
   return pl;
 }
