@@ -173,10 +173,12 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
 lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
                      float *proj, unsigned long long *counters, cudaStream_t stream);
 
-// Dense E2LSH / SRP (FP32 SIMT GEMM, fused discretisation and recheck).
+// Dense E2LSH / SRP (FP32 SIMT GEMM, fused discretisation; with p.queue
+// set, flagged entries are rechecked by a second kernel, else in place).
 // keys and multi-word SRP bits must be zeroed by the caller.
 cudaError_t launch_dense_fp32(const SketchLaunch &p, const float *G, const float *Gt, const float *gnorm,
                               cudaStream_t stream);
+int64_t dense_queue_cap(int64_t n, int64_t ML);
 
 // Dense E2LSH / SRP on the tensor cores (TMA + tcgen05, BF16 x BF16 -> FP32),
 // for BF16 rows and a family whose G is stored in BF16.

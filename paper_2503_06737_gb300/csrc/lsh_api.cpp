@@ -171,8 +171,21 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   if (kind_is_dense(d.kind)) {
     if (keys) LSH_CUDA_TRY(cudaMemsetAsync(keys, 0, sizeof(uint64_t) * size_t(key_ld) * d.L, stream));
     if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
-    LSH_CUDA_TRY(launch_dense_fp32(p, f->d_G, f->d_Gt, f->d_gnorm, stream));
-    count_launches(1);
+    // batches of 8192 rows or more queue their boundary rechecks for a second
+    // kernel (queue from the stream-ordered pool); smaller ones recheck in place
+    void *qbuf = nullptr;
+    if (X->n >= 8192) {
+      const int64_t qcap = dense_queue_cap(X->n, int64_t(d.m) * d.L);
+      LSH_CUDA_TRY(cudaMallocAsync(&qbuf, size_t(16 + 16 * qcap), stream));
+      p.qcount = static_cast<uint32_t *>(qbuf);
+      p.queue = reinterpret_cast<int4 *>(static_cast<char *>(qbuf) + 16);
+      p.qcap = uint32_t(qcap);
+      LSH_CUDA_TRY(cudaMemsetAsync(qbuf, 0, 16, stream));
+    }
+    const cudaError_t e = launch_dense_fp32(p, f->d_G, f->d_Gt, f->d_gnorm, stream);
+    if (qbuf) cudaFreeAsync(qbuf, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dense FP32 hash");
+    count_launches(qbuf ? 2 : 1);
     return LSH_OK;
   }
   if (X->rowptr) {

@@ -10,7 +10,7 @@ import torch
 
 from paper_2503_06737_gb300 import lsh, workloads
 
-from gpu_helpers import compare_hash
+from gpu_helpers import compare_hash, compare_keys_only
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,23 @@ def test_dense_parity(kind, n, d, m, L, dtype):
     X = workloads.gmm(n, d, 8, seed=n + d, device="cpu", dtype=dtype).cuda()
     stats, rel = compare_hash(dict(kind=kind, d=d, m=m, L=L, w=4.0, seed=13), X)
     assert stats["n_changed"] <= stats["n_flagged"]
+
+
+@pytest.mark.parametrize("kind", ["e2lsh", "srp"])
+def test_dense_fp32_queued_recheck(kind):
+    """Batches of 8192 rows or more queue their boundary rechecks for a second
+    kernel; narrow bins put many entries in the queue."""
+    fa = dict(kind=kind, d=200, m=16, L=8, w=0.05, seed=3)
+    X = workloads.gmm(9000, 200, 8, seed=7, device="cpu").cuda()
+    stats, _ = compare_hash(fa, X, check_proj=False)
+    assert stats["n_flagged"] > 0
+    compare_keys_only(fa, X)
+
+
+def test_dense_fp32_unaligned_rows():
+    """Rows that do not start on 16 bytes are staged one value at a time."""
+    X = workloads.gmm(300, 130, 8, seed=8, device="cpu").cuda()[:, 1:]
+    compare_hash(dict(kind="e2lsh", d=129, m=16, L=5, seed=4), X)
 
 
 def test_dense_narrow_bins_exercise_recheck():
