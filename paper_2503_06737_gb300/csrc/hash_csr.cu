@@ -32,6 +32,7 @@
 // this equals the dense definition).
 #include <algorithm>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,6 +51,7 @@ struct CsrArgs {
   const int32_t *col;
   const float *val;
   const uint16_t *colmajor;        // CS: [d][L] bin | neg << 15 (global)
+  const uint32_t *mseg;            // dense rows: [L][m][2] member records (word 1: n(+) | n(-) << 16)
   uint64_t dmagic[LSH_MAX_MODES];  // HCS: ceil(2^64 / d_k) (0 for d_k = 1)
   int stage;                       // entries staged in shared memory
   int tb;                          // tables per pass
@@ -125,12 +127,41 @@ __device__ __forceinline__ uint32_t lookup(const CsrArgs &a, const uint16_t *tab
   return bin | (neg << 31);
 }
 
+// Element e of the row being hashed.  SRC 0: the CSR row (column and value
+// of stored entry e); SRC 1 + dtype: a dense row of that element type, whose
+// entry e is coordinate e (xrow = row * ld).
+template <int SRC>
+__device__ __forceinline__ int nz_col(const CsrArgs &a, int64_t e) {
+  return SRC == 0 ? __ldg(a.col + e) : int(e);
+}
+template <int SRC>
+__device__ __forceinline__ float nz_val(const CsrArgs &a, int64_t xrow, int64_t e) {
+  if (SRC == 0) return __ldg(a.val + e);
+  if (SRC == 1 + LSH_F32) return __ldg(reinterpret_cast<const float *>(a.p.X) + xrow + e);
+  const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(a.p.X) + xrow + e);
+  if (SRC == 1 + LSH_BF16) return __uint_as_float(uint32_t(h) << 16);
+  return __half2float(__ushort_as_half(h));
+}
+
+// Error bound of bin l of table t: CSR rows, gamma_{nnz-1} ||v||_1 of the row
+// (rbound); dense rows, 1.02 gamma_{k-1} (1 + 2 gamma) k max|x| with k the
+// bin's member count (Higham, as for the dense-row kernel).
+template <int SRC>
+__device__ __forceinline__ float bin_bound(const CsrArgs &a, int t, int l, float rbound, float xmax) {
+  if (SRC == 0) return rbound;
+  const uint32_t w = __ldg(a.mseg + 2 * (int64_t(t) * a.p.m + l) + 1);
+  const float k = float((w & 0xffffu) + (w >> 16));
+  const float g = fmaxf(k - 1.f, 0.f) * kU32;
+  return 1.02f * g * (1.f + 2.f * g) * k * xmax;
+}
+
 // Exact FP64 value of bin l of table t of this warp's row (warp-collective;
 // every lane returns the same value).  nz: the warp's staged nonzeros {value
 // bits, lookup state}, lane's k-th at nz[32 k + lane] (kn of them), then the
 // row's nonzeros from position rs + 32 kReg on are read from global memory.
+template <int SRC>
 __device__ __noinline__ double exact_bin(const CsrArgs &a, const uint16_t *tab, int t, uint32_t l,
-                                         const uint2 *nz, int kn, int64_t rs, int64_t re, int lane) {
+                                         const uint2 *nz, int kn, int64_t rs, int64_t re, int64_t xrow, int lane) {
   const int64_t tail0 = rs + kWarp * kReg;
   int emin = 1 << 20, emax = -(1 << 20);
   for (int k = 0; k < kn; ++k) {
@@ -144,8 +175,8 @@ __device__ __noinline__ double exact_bin(const CsrArgs &a, const uint16_t *tab, 
     }
   }
   for (int64_t e = tail0 + lane; e < re; e += kWarp) {
-    const uint32_t u = __float_as_uint(a.val[e]);
-    if ((lookup(a, tab, t, prep_state(a, a.col[e])) & 0x7fffffffu) == l && (u & 0x7fffffffu)) {
+    const uint32_t u = __float_as_uint(nz_val<SRC>(a, xrow, e));
+    if ((lookup(a, tab, t, prep_state(a, nz_col<SRC>(a, e))) & 0x7fffffffu) == l && (u & 0x7fffffffu)) {
       const int E = max(int((u >> 23) & 0xff), 1) - 150;
       emin = min(emin, E);
       emax = max(emax, E);
@@ -173,8 +204,8 @@ __device__ __noinline__ double exact_bin(const CsrArgs &a, const uint16_t *tab, 
       if ((e & 0x7fffffffu) == l) add(z.x, e >> 31);
     }
     for (int64_t e = tail0 + lane; e < re; e += kWarp) {
-      const uint32_t en = lookup(a, tab, t, prep_state(a, a.col[e]));
-      if ((en & 0x7fffffffu) == l) add(__float_as_uint(a.val[e]), en >> 31);
+      const uint32_t en = lookup(a, tab, t, prep_state(a, nz_col<SRC>(a, e)));
+      if ((en & 0x7fffffffu) == l) add(__float_as_uint(nz_val<SRC>(a, xrow, e)), en >> 31);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -186,9 +217,9 @@ __device__ __noinline__ double exact_bin(const CsrArgs &a, const uint16_t *tab, 
   // the oracle's loop: ascending column order, one IEEE rounding per addition
   double y = 0.0;
   for (int64_t e = rs; e < re; ++e) {
-    const uint32_t en = lookup(a, tab, t, prep_state(a, a.col[e]));
+    const uint32_t en = lookup(a, tab, t, prep_state(a, nz_col<SRC>(a, e)));
     if ((en & 0x7fffffffu) == l) {
-      const double x = double(a.val[e]);
+      const double x = double(nz_val<SRC>(a, xrow, e));
       y = __dadd_rn(y, (en >> 31) ? -x : x);
     }
   }
@@ -224,9 +255,10 @@ __device__ __forceinline__ void scatter_one(const CsrArgs &a, const uint16_t *ta
 // are recomputed exactly by the whole warp, one at a time.  E2LSH and SRP
 // with m > 64 leave the lane's partial key sums in ha/hb; SRP with m <= 64
 // leaves the bit pattern itself (every lane the same).
-template <bool SRP>
+template <bool SRP, int SRC>
 __device__ __forceinline__ void epilogue_vec4(const CsrArgs &a, const uint16_t *tab, float *A, int64_t row, int t,
-                                              bool rowok, float Arow, float sq_w, uint32_t words, const uint2 *nz,
+                                              bool rowok, float Arow, float xmax, int64_t xrow, float sq_w,
+                                              uint32_t words, const uint2 *nz,
                                               int kn, int64_t rs, int64_t re, int lane, uint32_t &ha, uint32_t &hb,
                                               int &nflag, int &nchanged, int &novf) {
   const SketchLaunch &p = a.p;
@@ -248,7 +280,7 @@ __device__ __forceinline__ void epilogue_vec4(const CsrArgs &a, const uint16_t *
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const bool ez = __float_as_uint(y[k]) == 0x80000000u;  // exactly zero
-        const bool flag = rowok && inb && !ez && !(fabsf(y[k]) > Arow);
+        const bool flag = rowok && inb && !ez && !(fabsf(y[k]) > bin_bound<SRC>(a, t, l0 + k, Arow, xmax));
         fm |= uint32_t(flag) << k;
         code[k] = y[k] > 0.f ? 1 : 0;
       }
@@ -260,7 +292,8 @@ __device__ __forceinline__ void epilogue_vec4(const CsrArgs &a, const uint16_t *
         const bool ez = __float_as_uint(y[k]) == 0x80000000u;
         const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y[k], b[k]), a.invw_f);
         const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
-        const float M = fmaf(ez ? 0.f : sq_w, Arow, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
+        const float B = inb ? bin_bound<SRC>(a, t, l0 + k, Arow, xmax) : 0.f;
+        const float M = fmaf(ez ? 0.f : sq_w, B, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
         const bool flag = rowok && inb && !(dist > M);
         fm |= uint32_t(flag) << k;
         code[k] = __float2int_rd(tf);
@@ -276,7 +309,7 @@ __device__ __forceinline__ void epilogue_vec4(const CsrArgs &a, const uint16_t *
         const int k = __ffs(sfm) - 1;
         sfm &= sfm - 1;
         const int l = base + 4 * src + k;
-        const double y64 = exact_bin(a, tab, t, uint32_t(l), nz, kn, rs, re, lane);
+        const double y64 = exact_bin<SRC>(a, tab, t, uint32_t(l), nz, kn, rs, re, xrow, lane);
         if (lane == src) {
           int c64;
           if (SRP) {
@@ -340,8 +373,8 @@ __device__ __forceinline__ void epilogue_vec4(const CsrArgs &a, const uint16_t *
   }
 }
 
-template <bool SRP>
-__global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
+template <bool SRP, int SRC>
+__global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const __grid_constant__ CsrArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SketchLaunch &p = a.p;
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
@@ -364,7 +397,8 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
   const float sq_w = a.sqrtm_f * a.invw_f;
   const uint32_t words = uint32_t((m + 63) >> 6);
   for (int64_t row = int64_t(blockIdx.x) * nw + warp; row < p.n; row += nwarps) {
-    const int64_t rs = a.rowptr[row], re = a.rowptr[row + 1];
+    const int64_t rs = SRC == 0 ? a.rowptr[row] : 0, re = SRC == 0 ? a.rowptr[row + 1] : p.d;
+    const int64_t xrow = SRC == 0 ? 0 : row * p.ld;
     const int64_t nnz = re - rs;
     // ---- the row's first 32 kReg nonzeros into this warp's shared buffer
     // (all loads in flight first); validate the row and take ||v||_1 ----
@@ -373,12 +407,12 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
 #pragma unroll
     for (int k = 0; k < kReg; ++k) {
       const int64_t e = rs + lane + int64_t(k) * kWarp;
-      cc[k] = e < re ? __ldg(a.col + e) : 0;
-      xv[k] = e < re ? __ldg(a.val + e) : 0.f;
+      cc[k] = e < re ? nz_col<SRC>(a, e) : 0;
+      xv[k] = e < re ? nz_val<SRC>(a, xrow, e) : 0.f;
     }
     int kn = 0;
     bool ok = nnz >= 0;
-    float l1 = 0.f;
+    float l1 = 0.f, xmax = 0.f;
     int carry = -1;  // the column before this 32-chunk (lane 31 of the previous one)
 #pragma unroll
     for (int k = 0; k < kReg; ++k) {
@@ -391,18 +425,23 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
         ok = ok && c >= 0 && c < p.d && isfinite(xv[k]) && prev < c;
         nz[k * kWarp + lane] = make_uint2(__float_as_uint(xv[k]), (c >= 0 && c < p.d) ? prep_state(a, c) : 0u);
         l1 += fabsf(xv[k]);
+        xmax = fmaxf(xmax, fabsf(xv[k]));
         kn = k + 1;
       }
     }
     for (int64_t e = rs + kWarp * kReg + lane; e < re; e += kWarp) {
-      const int c = a.col[e];
-      const float x = a.val[e];
-      ok = ok && c >= 0 && c < p.d && isfinite(x) && a.col[e - 1] < c;
+      const int c = nz_col<SRC>(a, e);
+      const float x = nz_val<SRC>(a, xrow, e);
+      ok = ok && c >= 0 && c < p.d && isfinite(x) && (SRC != 0 || a.col[e - 1] < c);
       l1 += fabsf(x);
+      xmax = fmaxf(xmax, fabsf(x));
     }
     const bool rowok = __all_sync(0xffffffffu, ok);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+      xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
     const float gk = float(nnz > 1 ? nnz - 1 : 0) * kU32;
     // gamma_{nnz-1} ||v||_1 (2% slack) plus one flushed subnormal per term
     const float Arow = 1.02f * gk * (1.f + 2.f * gk) * l1 + float(nnz) * 1.1754944e-38f * 1.02f;
@@ -417,7 +456,7 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
           scatter_one(a, tab, acc, tb, nt, vec4, z.y, __uint_as_float(z.x));
         }
         for (int64_t e = rs + kWarp * kReg + lane; e < re; e += kWarp)
-          scatter_one(a, tab, acc, tb, nt, vec4, prep_state(a, a.col[e]), a.val[e]);
+          scatter_one(a, tab, acc, tb, nt, vec4, prep_state(a, nz_col<SRC>(a, e)), nz_val<SRC>(a, xrow, e));
       }
       __syncwarp();
       // ---- epilogue: lanes own bins ----
@@ -426,7 +465,8 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
         float *A = acc + tt * m;
         uint32_t ha = 0, hb = 0;
         if (vec4b) {
-          epilogue_vec4<SRP>(a, tab, A, row, t, rowok, Arow, sq_w, words, nz, kn, rs, re, lane, ha, hb, nflag,
+          epilogue_vec4<SRP, SRC>(a, tab, A, row, t, rowok, Arow, xmax, xrow, sq_w, words, nz, kn, rs, re, lane, ha,
+                                  hb, nflag,
                              nchanged, novf);
         } else {
         for (int base = 0; base < m; base += kWarp) {
@@ -439,13 +479,13 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
           }
           const bool ez = __float_as_uint(y) == 0x80000000u;  // exactly zero
           if (SRP) {
-            const bool flag = rowok && inb && !ez && !(fabsf(y) > Arow);
+            const bool flag = rowok && inb && !ez && !(fabsf(y) > bin_bound<SRC>(a, t, l, Arow, xmax));
             int bit = y > 0.f ? 1 : 0;
             uint32_t fm = __ballot_sync(0xffffffffu, flag);
             while (fm) {
               const int src = __ffs(fm) - 1;
               fm &= fm - 1;
-              const double y64 = exact_bin(a, tab, t, uint32_t(base + src), nz, kn, rs, re, lane);
+              const double y64 = exact_bin<SRC>(a, tab, t, uint32_t(base + src), nz, kn, rs, re, xrow, lane);
               if (lane == src) {
                 const int b64 = y64 > 0.0 ? 1 : 0;
                 ++nflag;
@@ -473,14 +513,15 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const CsrArgs a) {
             const float bl = inb ? __ldg(p.b32 + int64_t(t) * m + l) : 0.f;
             const float tf = __fmul_rn(__fmaf_rn(a.sqrtm_f, y, bl), a.invw_f);
             const float dist = fabsf(tf - rintf(tf));  // exact (Sterbenz)
-            const float M = fmaf(ez ? 0.f : sq_w, Arow, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
+            const float B = inb ? bin_bound<SRC>(a, t, l, Arow, xmax) : 0.f;
+            const float M = fmaf(ez ? 0.f : sq_w, B, fmaf(10.2f * kU32, fabsf(tf), 15.3f * kU32));
             const bool flag = rowok && inb && !(dist > M);
             int code = __float2int_rd(tf);
             uint32_t fm = __ballot_sync(0xffffffffu, flag);
             while (fm) {
               const int src = __ffs(fm) - 1;
               fm &= fm - 1;
-              const double y64 = exact_bin(a, tab, t, uint32_t(base + src), nz, kn, rs, re, lane);
+              const double y64 = exact_bin<SRC>(a, tab, t, uint32_t(base + src), nz, kn, rs, re, xrow, lane);
               if (lane == src) {
                 const double t1 = __dmul_rn(p.sqrtm, y64);
                 const double t2 = __dadd_rn(t1, p.b64[int64_t(t) * m + l]);
@@ -553,10 +594,18 @@ int sm_count() {
   return sms;
 }
 
+template <bool SRP, int SRC>
+cudaError_t launch_k(const CsrArgs &a, int grid, int W, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(sketch_csr_kernel<SRP, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
+  if (e != cudaSuccess) return e;
+  sketch_csr_kernel<SRP, SRC><<<grid, W * kWarp, a.smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
-                              const uint16_t *colmajor, cudaStream_t stream) {
+                              const uint16_t *colmajor, const uint32_t *mseg, cudaStream_t stream) {
   if (p.n <= 0) return cudaSuccess;
   CsrArgs a{};
   a.p = p;
@@ -564,6 +613,7 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
   a.col = col;
   a.val = val;
   a.colmajor = colmajor;
+  a.mseg = mseg;
   a.sqrtm_f = float(p.sqrtm);
   a.invw_f = float(1.0 / p.w);
   const bool cs = p.kind == LSH_CS_E2LSH || p.kind == LSH_CS_SRP;
@@ -601,17 +651,18 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
   const int64_t want = int64_t(sm_count()) * per_sm;
   const int64_t need = (p.n + W - 1) / W;
   const int grid = int(want < need ? want : need);
-  cudaError_t e;
-  if (kind_is_srp(p.kind)) {
-    e = cudaFuncSetAttribute(sketch_csr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
-    if (e != cudaSuccess) return e;
-    sketch_csr_kernel<true><<<grid, W * kWarp, a.smem, stream>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(sketch_csr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
-    if (e != cudaSuccess) return e;
-    sketch_csr_kernel<false><<<grid, W * kWarp, a.smem, stream>>>(a);
+  const int src = rowptr ? 0 : 1 + p.dtype;
+  if (!rowptr && (p.dtype < LSH_F32 || p.dtype > LSH_F16)) return cudaErrorInvalidValue;
+  const bool srp = kind_is_srp(p.kind);
+  switch (src) {
+    case 0: return srp ? launch_k<true, 0>(a, grid, W, stream) : launch_k<false, 0>(a, grid, W, stream);
+    case 1 + LSH_F32: return srp ? launch_k<true, 1 + LSH_F32>(a, grid, W, stream)
+                                 : launch_k<false, 1 + LSH_F32>(a, grid, W, stream);
+    case 1 + LSH_BF16: return srp ? launch_k<true, 1 + LSH_BF16>(a, grid, W, stream)
+                                  : launch_k<false, 1 + LSH_BF16>(a, grid, W, stream);
+    default: return srp ? launch_k<true, 1 + LSH_F16>(a, grid, W, stream)
+                        : launch_k<false, 1 + LSH_F16>(a, grid, W, stream);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lsh

@@ -164,9 +164,11 @@ void set_sketch_pin(const SketchPin &pin);
 bool sketch_pin_fits(int d, int m, int L, int cap);
 
 // CSR-row CS/HCS hashing (all L tables, one launch).  colmajor: count-sketch
-// tables as [d][L] entries bin | neg << 15 (NULL for HCS).
+// tables as [d][L] entries bin | neg << 15 (NULL for HCS).  With rowptr NULL
+// the rows are the dense rows p.X (p.dtype, p.ld) -- for d too large for the
+// dense-row kernel's tile -- bounded per bin with the member counts of mseg.
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
-                              const uint16_t *colmajor, cudaStream_t stream);
+                              const uint16_t *colmajor, const uint32_t *mseg, cudaStream_t stream);
 
 // Hash the rows of X into keys [L][key_ld] (+ optional codes, proj, counters);
 // stream-ordered, allocates nothing when counters is NULL.

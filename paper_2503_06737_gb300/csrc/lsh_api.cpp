@@ -190,14 +190,29 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   }
   if (X->rowptr) {
     if (d.N == 1 && d.m > 32768) return fail(LSH_EUNSUPPORTED, "CSR count-sketch path needs m <= 32768");
+    for (int k = 0; k < d.N; ++k)
+      if (d.mdims[k] > 32768) return fail(LSH_EUNSUPPORTED, "CSR HCS hashing needs mode sketch sizes <= 32768");
     if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
     LSH_CUDA_TRY(launch_sketch_csr(p, X->rowptr, X->col, static_cast<const float *>(X->values), f->d_colmajor,
-                                   stream));
+                                   f->d_mseg, stream));
     count_launches(1);
     return LSH_OK;
   }
   SketchPlan sp = plan_sketch_dense(d.d, d.m, d.L, f->sketch_cap, X->dtype);
-  if (!sp.ok) return fail(LSH_EUNSUPPORTED, "d too large for the shared-memory row tile of the dense kernel");
+  if (!sp.ok) {
+    // rows too long for the dense-row kernel's shared-memory tile: the warp-per-row
+    // kernel reads them in place (per-bin bounds need the member records, d < 65536)
+    const bool cs = d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP;
+    if (!f->d_mseg || (cs && !f->d_colmajor))
+      return fail(LSH_EUNSUPPORTED, "d too large for the dense-row kernel (and >= 65536 for the row-wise one)");
+    if (!cs)
+      for (int k = 0; k < d.N; ++k)
+        if (d.mdims[k] > 32768) return fail(LSH_EUNSUPPORTED, "row-wise HCS hashing needs mode sketch sizes <= 32768");
+    if (p.bits) LSH_CUDA_TRY(cudaMemsetAsync(p.bits, 0, size_t(X->n) * d.L * ((d.m + 63) / 64) * 8, stream));
+    LSH_CUDA_TRY(launch_sketch_csr(p, nullptr, nullptr, nullptr, f->d_colmajor, f->d_mseg, stream));
+    count_launches(1);
+    return LSH_OK;
+  }
   if (!sketch_pin_fits(d.d, d.m, d.L, f->sketch_cap))
     return fail(LSH_EUNSUPPORTED, "the pinned sketch plan (lsh_set_sketch_plan) does not fit this shape");
   if (p.bits && d.m > 64)  // multi-word SRP codes are assembled with atomic ORs

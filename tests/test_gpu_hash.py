@@ -269,3 +269,17 @@ def test_hash_every_plan(plan, kind, d, m, L, dims, mdims, dtype):
     _pinned(plan, lambda: compare_keys_only(fa, Xq))  # queued rechecks, keys only
     Xu = _rows(301, d + 1, seed=d, dtype=dtype, kind="gmm")[:, 1:]  # rows not 16-byte aligned
     _pinned(plan, lambda: compare_keys_only(fa, Xu))
+
+
+@pytest.mark.parametrize("kind,dims,mdims,dtype", [("cs_srp", None, None, torch.float32),
+                                                   ("cs_e2lsh", None, None, torch.bfloat16),
+                                                   ("hcs_e2lsh", [100, 100], [2, 4], torch.float32),
+                                                   ("hcs_srp", [100, 100], [4, 2], torch.float16)])
+def test_hash_long_rows(kind, dims, mdims, dtype):
+    """Rows too long for the dense-row kernel's shared-memory tile (d = 10,000,
+    the paper's Synthetic width) are hashed one warp per row in place, each bin
+    bounded by its member count times max |x|."""
+    fa = dict(kind=kind, d=10000, m=8, L=5, w=4.0, seed=9, dims=dims, mdims=mdims)
+    X = _rows(150, 10000, seed=31, dtype=dtype, kind="iid")
+    compare_hash(fa, X)
+    compare_keys_only(fa, _rows(700, 10000, seed=32, dtype=dtype, kind="iid"))
