@@ -55,7 +55,8 @@ typedef enum {
   LSH_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
   LSH_ENONFINITE = 5,    /* an input row held NaN or Inf: its codes and keys are not defined */
   LSH_EUNSUPPORTED = 6,  /* valid request the library does not implement */
-  LSH_ERANGE = 7         /* an E2LSH code fell outside int32 */
+  LSH_ERANGE = 7,        /* an E2LSH code fell outside int32 */
+  LSH_EIO = 8            /* a file could not be opened, read or written */
 } lsh_status;
 
 /* Hash kinds (numbering fixed: it is part of the ABI). */
@@ -322,6 +323,40 @@ lsh_status lsh_query(lsh_index_t idx, const lsh_matrix *Q, int32_t k, int32_t *i
 void lsh_index_destroy(lsh_index_t idx);
 
 /*
+ * Save an index's tables (and its kept rows, if any) to a file, and load them
+ * back (Sec. 3.1: the L hash tables are the index; the family is redrawn from
+ * its description, so the file stores only that description).
+ *   lsh_index_save  path: host string.  Synchronises the device; LSH_EIO when
+ *                   the file cannot be written.
+ *   lsh_index_load  fam must have the description the file was saved with
+ *                   (kind, d, m, L, modes, w, seed, compute), else LSH_EINVAL;
+ *                   *out receives a new index (owns its device memory).
+ *                   LSH_EIO for a missing or short file, LSH_EUNSUPPORTED for
+ *                   another file version.
+ * The file holds a versioned header, then nb [L] int64, offsets [L][n+1],
+ * ids [L][n] uint32, ukeys [L][n] uint64 and the rows [n][d] when kept, in the
+ * host's byte order.
+ */
+lsh_status lsh_index_save(lsh_index_t idx, const char *path);
+lsh_status lsh_index_load(lsh_family_t fam, const char *path, lsh_index_t *out);
+
+/*
+ * Merge per-shard top-k lists of an index sharded by rows (each shard an
+ * index over its own rows, ids local to the shard): the k best of the union
+ * by (distance, global id), global id = local id + id_offset[s].  Because a
+ * point's keys do not depend on the shard, a query's candidates over the
+ * whole database are the union of its candidates in the shards, so merging
+ * the shards' lsh_query results gives the unsharded result exactly.
+ *   ids[s], dist[s]  host [q][k] lists of shard s, ascending by (distance, id),
+ *                    -1 / +inf past their end (as lsh_query writes them).
+ *   out_ids          host int64 [q][k], -1 where fewer than k exist.
+ *   out_dist         host float [q][k], +inf there.
+ * Host only, no device use.
+ */
+lsh_status lsh_merge_topk(int32_t shards, int64_t q, int32_t k, const int32_t *const *ids,
+                          const float *const *dist, const int64_t *id_offset, int64_t *out_ids, float *out_dist);
+
+/*
  * Serving loop (continuous batching) around lsh_query, with the data and the
  * index resident on the device.  Requests are batches of host queries; a
  * scheduler thread admits the oldest waiting request whenever one of `slots`
@@ -384,8 +419,12 @@ void lsh_server_destroy(lsh_server_t srv);
  *   ids, ukeys, offsets, nbuckets
  *             device outputs laid out as in lsh_index_export ([L][n], [L][n],
  *             [L][n+1], [L]); the caller owns them.
- *   Limits: n * L <= LSH_STATIC_MAX_PAIRS (2^20); larger requests return
- *   LSH_EINVAL with a message.  The first call on a device looks up the
+ *   Limits: n * L <= LSH_STATIC_MAX_PAIRS (2^20), and the sort scratch --
+ *   keys twice (8 n L bytes each), ids (4 n L) and the digit histograms
+ *   (1024 ceil(n / 4096) L), each rounded up to 256 bytes -- at most 24 MiB;
+ *   so with few rows and many tables (n = 64, L = 16384, say) a request
+ *   within 2^20 pairs can still be refused.  Requests past either limit
+ *   return LSH_EINVAL with a message naming the limit.  The first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current;
  *   make that first call before any stream capture.  Every call uses the same
  *   array and leaves its contents behind, so calls that overlap on the GPU

@@ -104,6 +104,10 @@ SIGNATURES = [
     ("lsh_query", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, P, P,
                                  ctypes.POINTER(QueryStats), P]),
     ("lsh_index_destroy", None, [P]),
+    ("lsh_index_save", ctypes.c_int, [P, ctypes.c_char_p]),
+    ("lsh_index_load", ctypes.c_int, [P, ctypes.c_char_p, ctypes.POINTER(P)]),
+    ("lsh_merge_topk", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P),
+                                      ctypes.POINTER(P), P, P, P]),
     ("lsh_build_tables_static", ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P]),
     ("lsh_server_create", ctypes.c_int, [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
     ("lsh_server_submit", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -311,12 +315,42 @@ class Family:
             pass
 
 
+def load_index(family: "Family", path: str) -> "Index":
+    """Load an index saved with Index.save; the family must match the file's."""
+    h = ctypes.c_void_p()
+    _check(lib().lsh_index_load(family.handle, str(path).encode(), ctypes.byref(h)))
+    return Index(family, h)
+
+
+def merge_topk(ids_list, dist_list, id_offsets):
+    """Merge per-shard [q, k] top-k lists (numpy int32 / float32, ascending by
+    (distance, local id)) into the global top-k by (distance, global id):
+    returns (ids int64 [q, k], dist float32 [q, k]).  Host only."""
+    import numpy as np
+    S = len(ids_list)
+    ids_c = [np.ascontiguousarray(x, np.int32) for x in ids_list]
+    dst_c = [np.ascontiguousarray(x, np.float32) for x in dist_list]
+    q, k = ids_c[0].shape
+    offs = np.ascontiguousarray(id_offsets, np.int64)
+    ip = (ctypes.c_void_p * S)(*[a.ctypes.data for a in ids_c])
+    dp = (ctypes.c_void_p * S)(*[a.ctypes.data for a in dst_c])
+    out_i = np.empty((q, k), np.int64)
+    out_d = np.empty((q, k), np.float32)
+    _check(lib().lsh_merge_topk(S, q, k, ip, dp, ctypes.c_void_p(offs.ctypes.data),
+                                ctypes.c_void_p(out_i.ctypes.data), ctypes.c_void_p(out_d.ctypes.data)))
+    return out_i, out_d
+
+
 class Index:
     """The L hash tables over a batch of points (owns device memory)."""
 
     def __init__(self, family: Family, handle):
         self.family = family
         self.handle = handle
+
+    def save(self, path: str):
+        """Write the tables (and kept rows) to a file (lsh_index_save)."""
+        _check(lib().lsh_index_save(self.handle, str(path).encode()))
 
     def rebuild(self, X, stream=None):
         mtx = dense_matrix(X)

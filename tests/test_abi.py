@@ -113,3 +113,35 @@ def test_sketch_plan_pin_validation(L):
     for args in [(1, 4, 2, 25, 2), (4, 1, 1, 8, 4), (2, 2, 4, 1, 4)]:
         assert lib.lsh_set_sketch_plan(*args) == 0, args
     assert lib.lsh_set_sketch_plan(0, 0, 0, 0, 0) == 0
+
+
+def test_merge_topk_against_restatement(L):
+    """lsh_merge_topk (host only): the k best of the union by (distance,
+    global id), from sorted per-shard lists with -1 / +inf tails; ties in
+    distance across shards resolved by the global id."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    for shards, q, k in ((1, 5, 4), (3, 40, 10), (4, 7, 1)):
+        ids, dists, offs = [], [], []
+        for s in range(shards):
+            n_s = int(rng.integers(0, 2 * k))
+            cand = rng.choice(50, size=min(n_s, 50), replace=False)
+            dv = rng.integers(0, 6, size=(q, len(cand))).astype(np.float32) / 4  # many ties
+            ii = np.full((q, k), -1, np.int32)
+            dd = np.full((q, k), np.inf, np.float32)
+            for i in range(q):
+                order = sorted(range(len(cand)), key=lambda c: (dv[i, c], cand[c]))[:k]
+                ii[i, :len(order)] = cand[order]
+                dd[i, :len(order)] = dv[i, order]
+            ids.append(ii)
+            dists.append(dd)
+            offs.append(1000 * s)
+        got_i, got_d = L.merge_topk(ids, dists, offs)
+        for i in range(q):
+            pool = [(float(dists[s][i, j]), int(ids[s][i, j]) + offs[s]) for s in range(shards) for j in range(k)
+                    if ids[s][i, j] >= 0]
+            want = sorted(pool)[:k]
+            want += [(float("inf"), -1)] * (k - len(want))
+            assert [int(v) for v in got_i[i]] == [w[1] for w in want]
+            assert [float(v) for v in got_d[i]] == [w[0] for w in want]
+    assert L.lib().lsh_merge_topk(0, 1, 1, None, None, None, None, None) == 1  # LSH_EINVAL
