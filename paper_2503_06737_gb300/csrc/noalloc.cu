@@ -16,9 +16,11 @@
 
 namespace {
 
-// Scratch of the allocation-free build: 24 MiB, enough for the ping-pong
-// keys (8 B), ids (4 B) and digit histograms of up to 2^20 (point, table)
-// pairs.  Every GPU that loads this library holds it until the process exits.
+// Scratch of the allocation-free build: 24 MiB.  A request needs the
+// ping-pong keys (2 x 8 B) and ids (4 B) of its n L (point, table) pairs, at
+// most 2^20 of them (20 MiB), plus 1 KiB of digit histogram per 4096-row tile
+// and table; build_tables_scratch_bytes adds these up and larger requests are
+// refused.  Every GPU that loads this library holds it until the process exits.
 constexpr size_t kStaticScratchBytes = size_t(24) << 20;
 static __device__ __align__(256) unsigned char g_static_sort_scratch[kStaticScratchBytes];
 

@@ -55,3 +55,8 @@ def test_static_build_refuses_oversize():
     st = lib.lsh_build_tables_static(_p(dummy), n, L, _p(dummy), _p(dummy), _p(dummy), _p(dummy), None)
     assert st == 1  # LSH_EINVAL, before any device work
     assert b"LSH_STATIC_MAX_PAIRS" in lib.lsh_last_error()
+    # within 2^20 pairs, but the digit histograms of 16,384 one-tile tables
+    # take the scratch past 24 MiB
+    st = lib.lsh_build_tables_static(_p(dummy), 64, 16384, _p(dummy), _p(dummy), _p(dummy), _p(dummy), None)
+    assert st == 1
+    assert b"24 MiB" in lib.lsh_last_error()
