@@ -37,15 +37,15 @@ _SRC = os.path.join(_HERE, "lsh_oracle.c")
 _LIB = os.path.join(_HERE, "liblsh_oracle.so")
 
 # Kinds, in the numbering shared with the library's public header.
-E2LSH, SRP, CS_E2LSH, HCS_E2LSH, CS_SRP, HCS_SRP = range(6)
+E2LSH, SRP, CS_E2LSH, HCS_E2LSH, CS_SRP, HCS_SRP, CSL_SRP = range(7)
 KIND_NAMES = {"e2lsh": E2LSH, "srp": SRP, "cs_e2lsh": CS_E2LSH,
-              "hcs_e2lsh": HCS_E2LSH, "cs_srp": CS_SRP, "hcs_srp": HCS_SRP}
+              "hcs_e2lsh": HCS_E2LSH, "cs_srp": CS_SRP, "hcs_srp": HCS_SRP, "csl_srp": CSL_SRP}
 # Input dtypes: 0 f32, 1 bf16 (uint16 bits), 2 f16, 3 fp8 e4m3 (uint8 bits).
 F32, BF16, F16, E4M3 = range(4)
 
 
 def is_srp(kind: int) -> bool:
-    return kind in (SRP, CS_SRP, HCS_SRP)
+    return kind in (SRP, CS_SRP, HCS_SRP, CSL_SRP)
 
 
 def is_dense(kind: int) -> bool:
@@ -99,6 +99,8 @@ def _declare(L):
     L.orc_table_stream.argtypes = [U64, I32]
     L.orc_family_tables.restype = None
     L.orc_family_tables.argtypes = [U64, I32, I32, P, P, D, P, P, P, P, P]
+    L.orc_family_tables_l.restype = None
+    L.orc_family_tables_l.argtypes = [U64, I32, I32, I32, I32, D, P, P, P, P, P]
     L.orc_dense_family.restype = None
     L.orc_dense_family.argtypes = [U64, I32, I32, I32, D, I32, P, P, P, P]
     for nm in ("orc_from_bf16", "orc_from_f16"):
@@ -159,6 +161,7 @@ class Family:
     seed: int
     dims: list
     mdims: list
+    l: int = 1                        # CSSRP-L: nonzeros per column
     bins: np.ndarray | None = None    # [L, sum(dims)] int32
     signs: np.ndarray | None = None   # [L, sum(dims)] int8
     G: np.ndarray | None = None       # [d, m*L] float32 (dense kinds)
@@ -168,7 +171,7 @@ class Family:
 
     @property
     def N(self) -> int:
-        return len(self.dims)
+        return self.l if self.kind == CSL_SRP else len(self.dims)
 
     def mode_tables(self, t: int):
         """Per-mode (h_k, s_k) of table t as lists of arrays."""
@@ -181,7 +184,7 @@ class Family:
     def _c(self):
         f = _OrcFamily()
         f.kind, f.d, f.m, f.L, f.N = self.kind, self.d, self.m, self.L, self.N
-        for k in range(self.N):
+        for k in range(len(self.dims)):
             f.dims[k] = self.dims[k]
             f.mdims[k] = self.mdims[k]
         f.w = self.w
@@ -192,12 +195,22 @@ class Family:
         return f
 
 
-def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32) -> Family:
+def family(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32, l=1) -> Family:
     """Draw the family (Definitions 2-5) from `seed`.  CS kinds take dims=[d],
     mdims=[m]; HCS kinds take the mode sizes (prod(dims) >= d, prod(mdims) = m).
-    Dense kinds: compute = BF16 (E4M3) rounds every Gaussian entry to bfloat16 (FP8 E4M3)."""
+    Dense kinds: compute = BF16 (E4M3) rounds every Gaussian entry to bfloat16 (FP8 E4M3).
+    CSSRP-L ("csl_srp", Table 1): l distinct bins per coordinate, tables [L, d*l]."""
     kind = KIND_NAMES.get(kind, kind)
     lb = lib()
+    if kind == CSL_SRP:
+        assert 1 <= l <= m
+        bins = np.empty((L, d * l), np.int32)
+        signs = np.empty((L, d * l), np.int8)
+        b = np.empty((L, m), np.float64)
+        ka = np.empty((L, m), np.uint32)
+        kb = np.empty((L, m), np.uint32)
+        lb.orc_family_tables_l(seed, L, d, m, l, w, _p(bins), _p(signs), _p(b), _p(ka), _p(kb))
+        return Family(kind, d, m, L, float(w), seed, [d], [m], bins=bins, signs=signs, b=b, ka=ka, kb=kb, l=l)
     if is_dense(kind):
         G = np.empty((d, m * L), np.float32)
         b = np.empty((L, m), np.float64)

@@ -118,6 +118,50 @@ void orc_family_tables(uint64_t seed, int L, int N, const int32_t *dims,
   }
 }
 
+/*
+ * CSSRP-L family (Table 1: a count-sketch projection matrix with l nonzero
+ * entries in each column; the paper names it only by that property).
+ * Reading: coordinate i goes to l distinct bins h_1(i) .. h_l(i), each with
+ * its own random sign.  Draw order, per table t, from orc_table_stream(seed, t):
+ *   for i = 0..d-1, for r = 0..l-1: draws until the bin (hi32(r) * m) >> 32 is
+ *       not among the bins already chosen for i; the sign is bit31 of that
+ *       accepted draw (-1 when set, else +1);
+ *   then b_l and ka_l / kb_l exactly as in orc_family_tables.
+ * Output: bins/signs [L][d * l] (entry i * l + r), b [L][m], ka/kb [L][m].
+ * Needs 1 <= l <= m.
+ */
+void orc_family_tables_l(uint64_t seed, int L, int d, int m, int l, double w, int32_t *bins,
+                         int8_t *signs, double *b, uint32_t *ka, uint32_t *kb) {
+  const int64_t D = (int64_t)d * l;
+  for (int t = 0; t < L; ++t) {
+    uint64_t st = orc_table_stream(seed, t);
+    for (int i = 0; i < d; ++i) {
+      for (int r = 0; r < l; ++r) {
+        for (;;) {
+          uint64_t u = orc_splitmix_next(&st);
+          int32_t bin = orc_bucket(u, m);
+          int seen = 0;
+          for (int q = 0; q < r; ++q)
+            if (bins[t * D + (int64_t)i * l + q] == bin) seen = 1;
+          if (seen) continue;
+          bins[t * D + (int64_t)i * l + r] = bin;
+          signs[t * D + (int64_t)i * l + r] = orc_sign(u);
+          break;
+        }
+      }
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      uint64_t u = orc_splitmix_next(&st);
+      b[t * m + q] = w * orc_unit(u);
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      uint64_t u = orc_splitmix_next(&st);
+      ka[t * m + q] = (uint32_t)(u >> 32) | 1u;
+      kb[t * m + q] = (uint32_t)u | 1u;
+    }
+  }
+}
+
 /* Round a finite binary32 value to the nearest bfloat16 (8-bit significand),
  * ties to even, and return it as binary32. */
 static float orc_round_bf16(float f) {
@@ -256,6 +300,19 @@ void orc_cs_project(const double *x, int d, const int32_t *h, const int8_t *s,
   for (int i = 0; i < d; ++i) y[h[i]] = y[h[i]] + (double)s[i] * x[i];
 }
 
+/* CSSRP-L projection (Table 1): y_b = sum over (i, r) with h_r(i) = b of
+ * s_r(i) p_i.  One pass over i in ascending order adds each of its l terms
+ * into its bin, so every bin sums its own terms in ascending i. */
+void orc_csl_project(const double *x, int d, int l, const int32_t *h, const int8_t *s,
+                     int m, double *y) {
+  for (int q = 0; q < m; ++q) y[q] = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int r = 0; r < l; ++r) {
+      const int64_t e = (int64_t)i * l + r;
+      y[h[e]] = y[h[e]] + (double)s[e] * x[i];
+    }
+}
+
 /* Definition 5 with the vec() of Definitions 19/31.  The vector x of length d
  * is viewed as a d_1 x ... x d_N tensor with j = i_1 + i_2 d_1 + i_3 d_1 d_2 + ...
  * (first mode fastest); coordinates j >= d are the zero padding of Sec. 6.
@@ -343,7 +400,8 @@ uint64_t orc_key(const int32_t *codes, int m, int is_srp, const uint32_t *ka,
 /* ------------------------------------------------------------------ */
 
 /* kind codes: 0 E2LSH (dense), 1 SRP (dense), 2 CS-E2LSH, 3 HCS-E2LSH,
- *             4 CS-SRP, 5 HCS-SRP.  A count sketch is an HCS with N = 1. */
+ *             4 CS-SRP, 5 HCS-SRP, 6 CSSRP-L (N holds l, tables [L][d l]).
+ *             A count sketch is an HCS with N = 1. */
 typedef struct {
   int kind, d, m, L, N;
   int32_t dims[8], mdims[8];
@@ -355,16 +413,20 @@ typedef struct {
   const uint32_t *ka, *kb;
 } orc_family;
 
-static int orc_is_srp(int kind) { return kind == 1 || kind == 4 || kind == 5; }
+static int orc_is_srp(int kind) { return kind == 1 || kind == 4 || kind == 5 || kind == 6; }
 
 /* Projection of one point for table t (FP64, ascending j). */
 static void orc_project_table(const orc_family *f, const double *x, int t, double *y) {
   int64_t D = 0;
-  for (int k = 0; k < f->N; ++k) D += f->dims[k];
+  if (f->kind != 6)
+    for (int k = 0; k < f->N; ++k) D += f->dims[k];
   if (f->kind == 0 || f->kind == 1) {
     orc_dense_project(x, f->d, f->G, (int64_t)f->m * f->L, (int64_t)t * f->m, f->m, y);
   } else if (f->kind == 2 || f->kind == 4) {
     orc_cs_project(x, f->d, f->bins + t * D, f->signs + t * D, f->m, y);
+  } else if (f->kind == 6) {
+    const int64_t Dl = (int64_t)f->d * f->N;
+    orc_csl_project(x, f->d, f->N, f->bins + t * Dl, f->signs + t * Dl, f->m, y);
   } else {
     orc_hcs_project(x, f->d, f->N, f->dims, f->mdims, f->bins + t * D, f->signs + t * D, y);
   }

@@ -40,6 +40,10 @@ MUTANTS = [
      "a += (uint32_t)(uint16_t)codes[l] * ka[l];", "test_oracle_key.py"),
     ("key multiplier drawn from the low word", "ka[t * m + l] = (uint32_t)(r >> 32) | 1u;",
      "ka[t * m + l] = (uint32_t)r | 1u;", "test_oracle_key.py"),
+    ("CSSRP-L bins of a column not distinct", "if (seen) continue;", "if (seen && 0) continue;",
+     "test_oracle_csl.py"),
+    ("CSSRP-L sign dropped", "y[h[e]] = y[h[e]] + (double)s[e] * x[i];", "y[h[e]] = y[h[e]] + x[i];",
+     "test_oracle_csl.py"),
 ]
 
 
