@@ -66,7 +66,8 @@ typedef enum {
   LSH_CS_E2LSH = 2,   /* count sketch, scaled floor             (Definition 12) */
   LSH_HCS_E2LSH = 3,  /* higher-order count sketch, scaled floor (Definition 19) */
   LSH_CS_SRP = 4,     /* count sketch, sign                     (Definition 25) */
-  LSH_HCS_SRP = 5     /* higher-order count sketch, sign        (Definition 31) */
+  LSH_HCS_SRP = 5,    /* higher-order count sketch, sign        (Definition 31) */
+  LSH_CSL_SRP = 6     /* CSSRP-L: count-sketch matrix with l nonzeros per column, sign (Table 1) */
 } lsh_kind;
 
 /* Element types of inputs. */
@@ -104,6 +105,13 @@ typedef enum {
  *           ties to even: BF16 rows then run on the tensor cores) or
  *           LSH_FP8_E4M3 (rounded to E4M3, saturating at 448: per-row-scaled
  *           FP8 rows run on the tensor cores).  CS/HCS kinds ignore it.
+ *   nnz_per_col  CSSRP-L only: l, the nonzero entries per column of the
+ *           m x d sketch matrix (1 <= l <= m; 0 reads as 1): coordinate i
+ *           goes to l distinct bins, drawn in order per i as bin = (hi32(r) m)
+ *           >> 32, a draw whose bin i already has being drawn again, each with
+ *           its own sign bit31(r); the code is the sign of S x as for CS-SRP.
+ *           N = 1, dims = {d}, mdims = {m}.  Dense rows only (no CSR).  Other
+ *           kinds ignore it.
  */
 typedef struct {
   int32_t kind;
@@ -116,6 +124,7 @@ typedef struct {
   double w;
   uint64_t seed;
   int32_t compute;
+  int32_t nnz_per_col;
 } lsh_family_desc;
 
 /*
@@ -187,7 +196,8 @@ lsh_status lsh_family_describe(lsh_family_t fam, lsh_family_desc *desc);
 /*
  * Copy the family's tables to host buffers (any may be NULL):
  *   bins   [L][sum dims] int32   per-mode bucket hashes h_k, modes concatenated
- *   signs  [L][sum dims] int8    per-mode signs s_k
+ *                                (CSSRP-L: [L][d l], entry i l + r the r-th bin of i)
+ *   signs  [L][sum dims] int8    per-mode signs s_k (CSSRP-L: [L][d l])
  *   G      [d][m*L] float        dense kinds only
  *   b      [L][m] double         E2LSH offsets
  *   ka, kb [L][m] uint32         key multipliers
@@ -214,7 +224,9 @@ void lsh_family_destroy(lsh_family_t fam);
  *          with an E4M3 family, go to the tensor cores (the projection of an FP8
  *          row is its scale times the projection of its E4M3 values; FP8 rows
  *          need an E4M3 family, d and ld multiples of 16, 8 <= m <= 64 dividing
- *          64, m*L a multiple of 128, d <= 16384).  CSR inputs: CS/HCS kinds.
+ *          64 or E2LSH with m = 128, m*L a multiple of 128, d <= 16384).  CSR
+ *          inputs: CS/HCS kinds; dense rows too long for the dense-row kernel's
+ *          shared-memory tile (d up to 65535) are hashed row by row.
  *   codes  device, optional: E2LSH kinds int32 [n][L][m]; SRP kinds uint64
  *          [n][L][ceil(m/64)] with code l in bit (l % 64) of word l / 64.
  *   keys   device, optional: uint64 [L][n], the bucket key of (point, table):

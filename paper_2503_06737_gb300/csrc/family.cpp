@@ -106,6 +106,34 @@ void sample_family(const lsh_family_desc &d, HostFamily &hf) {
     }
     return;
   }
+  if (d.kind == LSH_CSL_SRP) {
+    // CSSRP-L: per coordinate i, l distinct bins in draw order (a draw whose
+    // bin i already has is drawn again), each with the sign of its draw
+    const int lc = incidences(d);
+    const int64_t dsum = int64_t(d.d) * lc;
+    hf.dsum = dsum;
+    hf.bins.assign(size_t(L) * dsum, 0);
+    hf.signs.assign(size_t(L) * dsum, 1);
+    for (int t = 0; t < L; ++t) {
+      Stream s(d.seed, t);
+      const int64_t base = int64_t(t) * dsum;
+      for (int i = 0; i < d.d; ++i)
+        for (int r = 0; r < lc; ++r) {
+          for (;;) {
+            const uint64_t u = s.next();
+            const int32_t bin = int32_t(((u >> 32) * uint64_t(uint32_t(m))) >> 32);
+            bool seen = false;
+            for (int q = 0; q < r; ++q) seen = seen || hf.bins[base + int64_t(i) * lc + q] == bin;
+            if (seen) continue;
+            hf.bins[base + int64_t(i) * lc + r] = bin;
+            hf.signs[base + int64_t(i) * lc + r] = (u & (1ULL << 31)) ? int8_t(-1) : int8_t(1);
+            break;
+          }
+        }
+      draw_offsets_and_keys(s, d, t, hf);
+    }
+    return;
+  }
   int64_t dsum = 0;
   for (int k = 0; k < d.N; ++k) dsum += d.dims[k];
   hf.dsum = dsum;
@@ -135,17 +163,21 @@ int sketch_capacity(const HostFamily &hf) {
     std::fill(cnt.begin(), cnt.end(), 0u);
     const int32_t *hb = hf.bins.data() + size_t(t) * hf.dsum;
     const int8_t *sb = hf.signs.data() + size_t(t) * hf.dsum;
-    for (int j = 0; j < d.d; ++j) {
-      int r = j, off = 0, stride = 1, bin = 0, neg = 0;
-      for (int k = 0; k < d.N; ++k) {
-        const int ik = r % d.dims[k];
-        r /= d.dims[k];
-        bin += hb[off + ik] * stride;
-        neg ^= sb[off + ik] < 0 ? 1 : 0;
-        stride *= d.mdims[k];
-        off += d.dims[k];
+    if (d.kind == LSH_CSL_SRP) {
+      for (int64_t e = 0; e < hf.dsum; ++e) ++cnt[size_t(2) * hb[e] + (sb[e] < 0 ? 1 : 0)];
+    } else {
+      for (int j = 0; j < d.d; ++j) {
+        int r = j, off = 0, stride = 1, bin = 0, neg = 0;
+        for (int k = 0; k < d.N; ++k) {
+          const int ik = r % d.dims[k];
+          r /= d.dims[k];
+          bin += hb[off + ik] * stride;
+          neg ^= sb[off + ik] < 0 ? 1 : 0;
+          stride *= d.mdims[k];
+          off += d.dims[k];
+        }
+        ++cnt[size_t(2) * bin + neg];
       }
-      ++cnt[size_t(2) * bin + neg];
     }
     int total = 0;
     for (int l = 0; l < d.m; ++l) {

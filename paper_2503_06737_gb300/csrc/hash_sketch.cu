@@ -99,7 +99,8 @@ struct EntFlags<uint32_t> {
 };
 constexpr int kMaxWpt = 4;  // warps per table at most; a table keeps kMaxWpt + 1 range records
 
-// Bin and sign of coordinate j in table t (per-mode tables, first mode fastest).
+// Bin and sign of entry j of table t: coordinate j (per-mode tables, first
+// mode fastest), or for CSSRP-L the incidence j = i l + r (the r-th bin of i).
 __device__ __forceinline__ void coord_bin(const SketchLaunch &p, int t, int j, int &bin, uint32_t &neg) {
   const uint16_t *hb = p.bins + int64_t(t) * p.dsum;
   const int8_t *sb = p.signs + int64_t(t) * p.dsum;
@@ -129,12 +130,14 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
                             uint4 *cst, uint2 *rng, int wpt, uint32_t *scratch, int lane) {
   const int d = p.d, m = p.m;
   uint32_t *cur = scratch;  // [2m]: counts, then write cursors (key = 2 bin + neg)
+  // incidences e = j lc + r: coordinate j's r-th bin (lc = 1 but for CSSRP-L)
+  const int lc = p.lc, ne = d * lc;
   for (int i = lane; i < 2 * m; i += kWarp) cur[i] = 0;
   __syncwarp();
-  for (int j = lane; j < d; j += kWarp) {
+  for (int e = lane; e < ne; e += kWarp) {
     int bin;
     uint32_t neg;
-    coord_bin(p, t, j, bin, neg);
+    coord_bin(p, t, e, bin, neg);
     atomicAdd(&cur[2 * bin + neg], 1u);
   }
   __syncwarp();
@@ -173,17 +176,17 @@ __device__ void stage_table(const SketchLaunch &p, int t, float a_scale, uint32_
   }
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
-  for (int base = 0; base < d; base += kWarp) {
-    const int j = base + lane;
-    const bool act = j < d;
+  for (int base = 0; base < ne; base += kWarp) {
+    const int e = base + lane;
+    const bool act = e < ne;
     const uint32_t amask = __ballot_sync(0xffffffffu, act);
     if (act) {
       int bin;
       uint32_t neg;
-      coord_bin(p, t, j, bin, neg);
+      coord_bin(p, t, e, bin, neg);
       const uint32_t key = 2u * uint32_t(bin) + neg;
       const uint32_t peers = __match_any_sync(amask, key);
-      ent[cur[key] + __popc(peers & lt)] = EntT(uint32_t(j) * unit);
+      ent[cur[key] + __popc(peers & lt)] = EntT(uint32_t(e / lc) * unit);
       __syncwarp(amask);
       if ((peers & lt) == 0) cur[key] += __popc(peers);
     }
@@ -1054,7 +1057,7 @@ __global__ void __launch_bounds__(256) sketch_recheck_kernel(const SketchLaunch 
     const int t = r.y, l = r.z;
     const int64_t tl = int64_t(t) * p.m + l;
     const uint32_t start = mseg[2 * tl], np = mseg[2 * tl + 1] & 0xFFFFu, nn = mseg[2 * tl + 1] >> 16;
-    const uint16_t *P = mlist + int64_t(t) * p.d + start;
+    const uint16_t *P = mlist + int64_t(t) * p.d * p.lc + start;
     const uint16_t *N = P + np;
     const int64_t xb = row * p.ld;
     // exact path

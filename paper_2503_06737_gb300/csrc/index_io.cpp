@@ -4,7 +4,8 @@
 // File layout (little-endian, the host's native integer and IEEE layouts):
 //   header   magic "LSHGB300", u32 version (1), u32 header bytes,
 //            the family description (kind, d, m, L, N, dims[8], mdims[8],
-//            w, seed, compute), i64 n, i64 d, i32 data dtype, i32 has data
+//            w, seed, compute, l of CSSRP-L or 0), i64 n, i64 d,
+//            i32 data dtype, i32 has data
 //   nb       i64 [L]           buckets per table
 //   offsets  u32 [L][n+1]      bucket starts
 //   ids      u32 [L][n]        point ids in (key, id) order
@@ -37,7 +38,7 @@ struct FileHeader {
   int32_t dims[LSH_MAX_MODES], mdims[LSH_MAX_MODES];
   double w;
   uint64_t seed;
-  int32_t compute, pad0;
+  int32_t compute, nnz_per_col;
   int64_t n, dcols;
   int32_t data_dtype, has_data;
 };
@@ -77,6 +78,7 @@ bool same_family(const lsh_family_desc &a, const FileHeader &h) {
   if (a.kind != h.kind || a.d != h.d || a.m != h.m || a.L != h.L || a.N != h.N || a.seed != h.seed ||
       a.compute != h.compute || !(a.w == h.w))
     return false;
+  if (h.nnz_per_col != (a.kind == LSH_CSL_SRP ? incidences(a) : 0)) return false;
   for (int k = 0; k < a.N && k < LSH_MAX_MODES; ++k)
     if (a.dims[k] != h.dims[k] || a.mdims[k] != h.mdims[k]) return false;
   return true;
@@ -110,6 +112,7 @@ lsh_status lsh_index_save(lsh_index_t idx, const char *path) {
   h.w = fd.w;
   h.seed = fd.seed;
   h.compute = fd.compute;
+  h.nnz_per_col = fd.kind == LSH_CSL_SRP ? incidences(fd) : 0;
   h.n = idx->n;
   h.dcols = idx->d;
   h.has_data = idx->d_data ? 1 : 0;
@@ -149,7 +152,7 @@ lsh_status lsh_index_load(lsh_family_t fam, const char *path, lsh_index_t *out) 
     return fail(LSH_EUNSUPPORTED, "lsh_index_load: unknown file version");
   if (!same_family(fam->host.desc, h))
     return fail(LSH_EINVAL, "lsh_index_load: the file was built with another family (kind, d, m, L, modes, w, "
-                            "seed or compute differ)");
+                            "seed, compute or nnz_per_col differ)");
   if (h.n < 0 || h.n > int64_t(UINT32_MAX) - 1 || h.dcols != h.d)
     return fail(LSH_EINVAL, "lsh_index_load: corrupt header");
   if (h.has_data && (h.data_dtype < LSH_F32 || h.data_dtype > LSH_F16))

@@ -34,7 +34,11 @@ enum : uint32_t { STATUS_NONFINITE = 1u, STATUS_OVERFLOW = 2u, STATUS_TIMEOUT = 
 // Per-call device counters (order matches lsh_hash_stats after n_entries).
 enum { CNT_FLAGGED = 0, CNT_CHANGED = 1, CNT_NONFINITE = 2, CNT_OVERFLOW = 3, CNT_NUM = 8 };
 
-inline bool kind_is_srp(int k) { return k == LSH_SRP || k == LSH_CS_SRP || k == LSH_HCS_SRP; }
+inline bool kind_is_srp(int k) { return k == LSH_SRP || k == LSH_CS_SRP || k == LSH_HCS_SRP || k == LSH_CSL_SRP; }
+// Entries of a coordinate in one table: l for CSSRP-L, else 1.
+inline int incidences(const lsh_family_desc &d) {
+  return d.kind == LSH_CSL_SRP && d.nnz_per_col > 1 ? d.nnz_per_col : 1;
+}
 inline bool kind_is_dense(int k) { return k == LSH_E2LSH || k == LSH_SRP; }
 inline bool kind_is_sketch(int k) { return !kind_is_dense(k); }
 inline bool kind_scaled(int k) { return k == LSH_CS_E2LSH || k == LSH_HCS_E2LSH; }
@@ -45,7 +49,7 @@ inline bool kind_scaled(int k) { return k == LSH_CS_E2LSH || k == LSH_HCS_E2LSH;
 struct HostFamily {
   lsh_family_desc desc;
   int64_t dsum = 0;               // sum of mode sizes
-  std::vector<int32_t> bins;      // [L][dsum]
+  std::vector<int32_t> bins;      // [L][dsum] (CSSRP-L: dsum = d l, entry i l + r)
   std::vector<int8_t> signs;      // [L][dsum]
   std::vector<float> G;           // [d][m*L] dense kinds
   std::vector<double> b;          // [L][m]
@@ -91,7 +95,7 @@ struct lsh_family_s {
   int device = 0;
   int sketch_cap = 0;             // see lsh::sketch_capacity
   uint16_t *d_colmajor = nullptr; // CS kinds: [d][L] bin | neg << 15 (CSR path)
-  uint16_t *d_mlist = nullptr;    // CS/HCS, d < 65536: [L][d] coordinates by (bin, sign, j)
+  uint16_t *d_mlist = nullptr;    // CS/HCS, d < 65536: [L][d lc] coordinates by (bin, sign, j)
   uint32_t *d_mseg = nullptr;     // [L][m][2]: start in the table's list, n(+) | n(-) << 16
 };
 
@@ -124,7 +128,8 @@ struct SketchLaunch {
   // family
   int32_t kind, m, L, N;
   int32_t dims[LSH_MAX_MODES], mdims[LSH_MAX_MODES];
-  int32_t dsum;
+  int32_t dsum;          // entries per table of bins/signs (sum of mode sizes; CSSRP-L: d l)
+  int32_t lc;            // entries per coordinate (CSSRP-L: l, else 1)
   int32_t cap;           // staged member-list capacity per table (sketch_capacity)
   const uint16_t *bins;
   const int8_t *signs;

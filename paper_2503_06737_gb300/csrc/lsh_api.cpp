@@ -33,7 +33,11 @@ lsh_status cuda_fail(cudaError_t e, const char *what) {
 namespace {
 
 lsh_status validate_desc(const lsh_family_desc &d) {
-  if (d.kind < LSH_E2LSH || d.kind > LSH_HCS_SRP) return fail(LSH_EINVAL, "unknown kind");
+  if (d.kind < LSH_E2LSH || d.kind > LSH_CSL_SRP) return fail(LSH_EINVAL, "unknown kind");
+  if (d.kind == LSH_CSL_SRP) {
+    if (d.nnz_per_col < 0 || d.nnz_per_col > d.m) return fail(LSH_EINVAL, "CSSRP-L needs 1 <= nnz_per_col <= m");
+    if (int64_t(d.d) * incidences(d) >= (int64_t(1) << 31)) return fail(LSH_EINVAL, "d * nnz_per_col too large");
+  }
   if (d.d < 1) return fail(LSH_EINVAL, "d must be >= 1");
   if (d.m < 1) return fail(LSH_EINVAL, "m must be >= 1");
   if (d.L < 1) return fail(LSH_EINVAL, "L must be >= 1");
@@ -55,7 +59,7 @@ lsh_status validate_desc(const lsh_family_desc &d) {
   }
   if (M != d.m) return fail(LSH_EINVAL, "prod(mdims) must equal m");
   if (D < d.d) return fail(LSH_EINVAL, "prod(dims) must be >= d");
-  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP) && (d.N != 1 || d.dims[0] != d.d))
+  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP || d.kind == LSH_CSL_SRP) && (d.N != 1 || d.dims[0] != d.d))
     return fail(LSH_EINVAL, "CS kinds take N = 1, dims = {d}, mdims = {m}");
   if (d.m > 65535) return fail(LSH_EINVAL, "m must be < 65536");
   return LSH_OK;
@@ -123,7 +127,8 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
   if (X->dtype == LSH_FP8_E4M3 && !(f->d_Gt8 && tc_dense_supported(d, X)))
     return fail(LSH_EUNSUPPORTED, "FP8 rows are hashed by dense families with an FP8 G on the tensor cores "
-                                  "(d <= 16384 and the row stride multiples of 16, m in 8..64 dividing 64, m*L a multiple of 128)");
+                                  "(d <= 16384 and the row stride multiples of 16, m in 8..64 dividing 64 or E2LSH with m = 128, "
+                                  "m*L a multiple of 128)");
   SketchLaunch p{};
   p.X = X->values;
   p.row_scale = X->row_scale;
@@ -140,6 +145,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
     p.mdims[k] = d.mdims[k];
   }
   p.dsum = int32_t(f->host.dsum);
+  p.lc = incidences(d);
   p.cap = f->sketch_cap;
   p.bins = f->d_bins;
   p.signs = f->d_signs;
@@ -188,6 +194,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
     count_launches(qbuf ? 2 : 1);
     return LSH_OK;
   }
+  if (X->rowptr && d.kind == LSH_CSL_SRP) return fail(LSH_EUNSUPPORTED, "CSSRP-L hashes dense rows only");
   if (X->rowptr) {
     if (d.N == 1 && d.m > 32768) return fail(LSH_EUNSUPPORTED, "CSR count-sketch path needs m <= 32768");
     for (int k = 0; k < d.N; ++k)
@@ -203,6 +210,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
     // rows too long for the dense-row kernel's shared-memory tile: the warp-per-row
     // kernel reads them in place (per-bin bounds need the member records, d < 65536)
     const bool cs = d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP;
+    if (d.kind == LSH_CSL_SRP) return fail(LSH_EUNSUPPORTED, "CSSRP-L rows must fit the dense-row kernel's tile");
     if (!f->d_mseg || (cs && !f->d_colmajor))
       return fail(LSH_EUNSUPPORTED, "d too large for the dense-row kernel (and >= 65536 for the row-wise one)");
     if (!cs)
@@ -241,7 +249,8 @@ namespace {
 
 lsh_family_desc normalized(const lsh_family_desc &in) {
   lsh_family_desc d = in;
-  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP || kind_is_dense(d.kind)) && d.N == 0) {
+  if ((d.kind == LSH_CS_E2LSH || d.kind == LSH_CS_SRP || d.kind == LSH_CSL_SRP || kind_is_dense(d.kind)) &&
+      d.N == 0) {
     d.N = 1;
     d.dims[0] = d.d;
     d.mdims[0] = d.m;
@@ -428,7 +437,7 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
     }
 
   }
-  if (e == cudaSuccess && kind_is_sketch(d.kind) && d.N == 1 && d.m <= 32768) {
+  if (e == cudaSuccess && kind_is_sketch(d.kind) && d.kind != LSH_CSL_SRP && d.N == 1 && d.m <= 32768) {
     // column-major copy of the count-sketch tables for the CSR kernel
     std::vector<uint16_t> cm(size_t(d.d) * d.L);
     for (int t = 0; t < d.L; ++t)
@@ -441,25 +450,34 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
   if (e == cudaSuccess && kind_is_sketch(d.kind) && d.d < 65536) {
     // per-table member lists for the deferred recheck: the coordinates of each
     // bin with s = +1 in ascending j, then those with s = -1
-    std::vector<uint16_t> ml(size_t(d.L) * d.d);
+    // (CSSRP-L: one entry per (coordinate, bin) incidence, lc per coordinate)
+    const int lc = incidences(d);
+    const int64_t D = int64_t(d.d) * lc;
+    std::vector<uint16_t> ml(size_t(d.L) * D);
     std::vector<uint32_t> ms(size_t(d.L) * d.m * 2);
-    std::vector<int> bin(d.d), neg(d.d);
+    std::vector<int> bin(D), neg(D);
     std::vector<uint32_t> cnt(size_t(2) * d.m), cur(size_t(2) * d.m);
     for (int t = 0; t < d.L; ++t) {
       std::fill(cnt.begin(), cnt.end(), 0u);
-      for (int j = 0; j < d.d; ++j) {
-        int r = j, off = 0, stride = 1, bn = 0, ng = 0;
-        for (int k = 0; k < d.N; ++k) {
-          const int ik = r % d.dims[k];
-          r /= d.dims[k];
-          const size_t src = size_t(t) * h.dsum + off + ik;
-          bn += h.bins[src] * stride;
-          ng ^= h.signs[src] < 0 ? 1 : 0;
-          stride *= d.mdims[k];
-          off += d.dims[k];
+      for (int64_t e = 0; e < D; ++e) {
+        int bn = 0, ng = 0;
+        if (d.kind == LSH_CSL_SRP) {
+          bn = h.bins[size_t(t) * h.dsum + e];
+          ng = h.signs[size_t(t) * h.dsum + e] < 0 ? 1 : 0;
+        } else {
+          int r = int(e), off = 0, stride = 1;
+          for (int k = 0; k < d.N; ++k) {
+            const int ik = r % d.dims[k];
+            r /= d.dims[k];
+            const size_t src = size_t(t) * h.dsum + off + ik;
+            bn += h.bins[src] * stride;
+            ng ^= h.signs[src] < 0 ? 1 : 0;
+            stride *= d.mdims[k];
+            off += d.dims[k];
+          }
         }
-        bin[j] = bn;
-        neg[j] = ng;
+        bin[e] = bn;
+        neg[e] = ng;
         ++cnt[size_t(2) * bn + ng];
       }
       uint32_t start = 0;
@@ -470,7 +488,7 @@ lsh_status lsh_make_family(const lsh_family_desc *desc, lsh_family_t *out) {
         cur[2 * l + 1] = start + cnt[2 * l];
         start += cnt[2 * l] + cnt[2 * l + 1];
       }
-      for (int j = 0; j < d.d; ++j) ml[size_t(t) * d.d + cur[size_t(2) * bin[j] + neg[j]]++] = uint16_t(j);
+      for (int64_t e = 0; e < D; ++e) ml[size_t(t) * D + cur[size_t(2) * bin[e] + neg[e]]++] = uint16_t(e / lc);
     }
     e = upload(&f->d_mlist, ml.data(), ml.size());
     if (e == cudaSuccess) e = upload(&f->d_mseg, ms.data(), ms.size());

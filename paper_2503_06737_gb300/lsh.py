@@ -16,9 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblsh_gb300.so")
 
 # Kinds and dtypes: the numbering of lsh_kind / lsh_dtype.
-E2LSH, SRP, CS_E2LSH, HCS_E2LSH, CS_SRP, HCS_SRP = range(6)
+E2LSH, SRP, CS_E2LSH, HCS_E2LSH, CS_SRP, HCS_SRP, CSL_SRP = range(7)
 KINDS = {"e2lsh": E2LSH, "srp": SRP, "cs_e2lsh": CS_E2LSH, "hcs_e2lsh": HCS_E2LSH,
-         "cs_srp": CS_SRP, "hcs_srp": HCS_SRP}
+         "cs_srp": CS_SRP, "hcs_srp": HCS_SRP, "csl_srp": CSL_SRP}
 F32, BF16, F16, FP8_E4M3 = range(4)
 _TORCH_DTYPE = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.uint8: FP8_E4M3,
                 torch.float8_e4m3fn: FP8_E4M3}
@@ -38,7 +38,8 @@ class FamilyDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("dims", ctypes.c_int32 * MAX_MODES), ("mdims", ctypes.c_int32 * MAX_MODES),
-                ("w", ctypes.c_double), ("seed", ctypes.c_uint64), ("compute", ctypes.c_int32)]
+                ("w", ctypes.c_double), ("seed", ctypes.c_uint64), ("compute", ctypes.c_int32),
+                ("nnz_per_col", ctypes.c_int32)]
 
 
 class Matrix(ctypes.Structure):
@@ -185,7 +186,7 @@ def csr_matrix(rowptr: torch.Tensor, col: torch.Tensor, values: torch.Tensor, d:
     return mtx
 
 
-def make_desc(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32) -> FamilyDesc:
+def make_desc(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32, l=1) -> FamilyDesc:
     desc = FamilyDesc()
     desc.kind = KINDS.get(kind, kind)
     desc.d, desc.m, desc.L = d, m, L
@@ -198,15 +199,16 @@ def make_desc(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32)
     desc.w = float(w)
     desc.seed = int(seed)
     desc.compute = compute
+    desc.nnz_per_col = int(l)
     return desc
 
 
-def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32):
+def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32, l=1):
     """The library's host sampler alone (no device): dict of numpy tables."""
     import numpy as np
-    desc = make_desc(kind, d, m, L, w, seed, dims, mdims, compute)
+    desc = make_desc(kind, d, m, L, w, seed, dims, mdims, compute, l)
     dense = desc.kind in (E2LSH, SRP)
-    dsum = 0 if dense else sum(desc.dims[k] for k in range(desc.N))
+    dsum = 0 if dense else (d * max(1, l) if desc.kind == CSL_SRP else sum(desc.dims[k] for k in range(desc.N)))
     bins = np.empty((L, dsum), np.int32)
     signs = np.empty((L, dsum), np.int8)
     G = np.empty((d, m * L), np.float32) if dense else None
@@ -221,33 +223,25 @@ def sample_family_tables(kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, c
 class Family:
     """An LSH family drawn on the host and resident on the current device."""
 
-    def __init__(self, kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32):
-        desc = FamilyDesc()
-        desc.kind = KINDS.get(kind, kind)
-        desc.d, desc.m, desc.L = d, m, L
+    def __init__(self, kind, d, m, L, w=4.0, seed=42, dims=None, mdims=None, compute=F32, l=1):
+        desc = make_desc(kind, d, m, L, w, seed, dims, mdims, compute, l)
         if dims is None:
             dims, mdims = [d], [m]
-        desc.N = len(dims)
-        for k, (a, b) in enumerate(zip(dims, mdims)):
-            desc.dims[k] = a
-            desc.mdims[k] = b
-        desc.w = float(w)
-        desc.seed = int(seed)
-        desc.compute = compute
         h = ctypes.c_void_p()
         _check(lib().lsh_make_family(ctypes.byref(desc), ctypes.byref(h)))
         self.handle = h
+        self.l = max(1, int(l))
         self.kind, self.d, self.m, self.L, self.w, self.seed = desc.kind, d, m, L, float(w), seed
         self.dims, self.mdims = list(dims), list(mdims)
 
     @property
     def is_srp(self):
-        return self.kind in (SRP, CS_SRP, HCS_SRP)
+        return self.kind in (SRP, CS_SRP, HCS_SRP, CSL_SRP)
 
     def export(self):
         """Host copies of the drawn tables (for parity checks)."""
         import numpy as np
-        dsum = sum(self.dims) if self.kind not in (E2LSH, SRP) else 0
+        dsum = 0 if self.kind in (E2LSH, SRP) else (self.d * self.l if self.kind == CSL_SRP else sum(self.dims))
         bins = np.empty((self.L, dsum), np.int32)
         signs = np.empty((self.L, dsum), np.int8)
         G = np.empty((self.d, self.m * self.L), np.float32) if self.kind in (E2LSH, SRP) else None

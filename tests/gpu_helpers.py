@@ -45,7 +45,7 @@ def compare_hash(fam_args: dict, X: torch.Tensor, rows=None, check_proj=True):
     ofam = oracle.family(fam_args["kind"], fam_args["d"], fam_args["m"], fam_args["L"],
                          w=fam_args.get("w", 4.0), seed=fam_args.get("seed", 42),
                          dims=fam_args.get("dims"), mdims=fam_args.get("mdims"),
-                         compute=fam_args.get("compute", 0))
+                         compute=fam_args.get("compute", 0), l=fam_args.get("l", 1))
     st, y, codes, keys = oracle.hash_dense(ofam, Xh, dtype=dt)
     assert st == 0
     m = fam_args["m"]
@@ -76,7 +76,7 @@ def oracle_keys(fam_args: dict, X: torch.Tensor):
     ofam = oracle.family(fam_args["kind"], fam_args["d"], fam_args["m"], fam_args["L"],
                          w=fam_args.get("w", 4.0), seed=fam_args.get("seed", 42),
                          dims=fam_args.get("dims"), mdims=fam_args.get("mdims"),
-                         compute=fam_args.get("compute", 0))
+                         compute=fam_args.get("compute", 0), l=fam_args.get("l", 1))
     st, _, _, keys = oracle.hash_dense(ofam, Xh, dtype=dt, want_y=False, want_codes=False)
     assert st == 0
     return keys

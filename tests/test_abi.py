@@ -145,3 +145,15 @@ def test_merge_topk_against_restatement(L):
             assert [int(v) for v in got_i[i]] == [w[1] for w in want]
             assert [float(v) for v in got_d[i]] == [w[0] for w in want]
     assert L.lib().lsh_merge_topk(0, 1, 1, None, None, None, None, None) == 1  # LSH_EINVAL
+
+
+@pytest.mark.parametrize("d,m,l", [(40, 16, 3), (960, 64, 2), (128, 8, 8)])
+def test_csl_sampler_equals_oracle(L, d, m, l):
+    """The library's CSSRP-L draws (l distinct bins per coordinate, by
+    rejection) equal the oracle's independent draw."""
+    import numpy as np
+    import oracle
+    t = L.sample_family_tables("csl_srp", d, m, 4, seed=17, l=l)
+    o = oracle.family("csl_srp", d, m, 4, seed=17, l=l)
+    for key in ("bins", "signs", "b", "ka", "kb"):
+        assert np.array_equal(t[key], getattr(o, key)), key

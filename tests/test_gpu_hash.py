@@ -283,3 +283,18 @@ def test_hash_long_rows(kind, dims, mdims, dtype):
     X = _rows(150, 10000, seed=31, dtype=dtype, kind="iid")
     compare_hash(fa, X)
     compare_keys_only(fa, _rows(700, 10000, seed=32, dtype=dtype, kind="iid"))
+
+
+@pytest.mark.parametrize("d,m,l,L,n,dtype", [(960, 64, 2, 7, 700, torch.float32), (128, 16, 4, 9, 9001, torch.float16),
+                                            (300, 96, 3, 3, 500, torch.bfloat16), (64, 8, 8, 5, 129, torch.float32)])
+def test_hash_csl_srp(d, m, l, L, n, dtype):
+    """CSSRP-L (Table 1): each coordinate in l distinct bins of every table;
+    codes and keys against the oracle (9,001 rows: queued rechecks), and
+    with every plan shape pinned on the first case."""
+    fa = dict(kind="csl_srp", d=d, m=m, L=L, seed=23, l=l)
+    X = _rows(n, d, seed=d + l, dtype=dtype, kind="gmm")
+    compare_hash(fa, X)
+    compare_keys_only(fa, X)
+    if d == 960:
+        for plan in PLANS:
+            _pinned(plan, lambda: compare_keys_only(fa, X))

@@ -10,15 +10,16 @@ from paper_2503_06737_gb300 import lsh, workloads
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind,dims,mdims,dtype", [("cs_e2lsh", None, None, torch.float32),
-                                                   ("hcs_srp", [8, 8], [4, 4], torch.float16)])
-def test_save_load_roundtrip(tmp_path, kind, dims, mdims, dtype):
+@pytest.mark.parametrize("kind,dims,mdims,dtype,l", [("cs_e2lsh", None, None, torch.float32, 1),
+                                                     ("hcs_srp", [8, 8], [4, 4], torch.float16, 1),
+                                                     ("csl_srp", None, None, torch.float32, 3)])
+def test_save_load_roundtrip(tmp_path, kind, dims, mdims, dtype, l):
     X = workloads.gmm(5000, 64, 8, seed=21, device="cpu", dtype=dtype).cuda()
-    fam = lsh.Family(kind, 64, 16, 6, w=4.0, seed=5, dims=dims, mdims=mdims)
+    fam = lsh.Family(kind, 64, 16, 6, w=4.0, seed=5, dims=dims, mdims=mdims, l=l)
     idx = fam.build_index(X, keep_data=True)
     path = tmp_path / "index.bin"
     idx.save(path)
-    fam2 = lsh.Family(kind, 64, 16, 6, w=4.0, seed=5, dims=dims, mdims=mdims)
+    fam2 = lsh.Family(kind, 64, 16, 6, w=4.0, seed=5, dims=dims, mdims=mdims, l=l)
     loaded = lsh.load_index(fam2, path)
     a, b = idx.export(), loaded.export()
     for key in ("ids", "nb", "offsets"):
@@ -34,6 +35,10 @@ def test_save_load_roundtrip(tmp_path, kind, dims, mdims, dtype):
     with pytest.raises(lsh.LshError) as e:
         lsh.load_index(other, path)
     assert e.value.status == 1  # LSH_EINVAL: another family
+    if kind == "csl_srp":
+        with pytest.raises(lsh.LshError) as e:
+            lsh.load_index(lsh.Family(kind, 64, 16, 6, w=4.0, seed=5, l=2), path)
+        assert e.value.status == 1  # another number of nonzeros per column
     with pytest.raises(lsh.LshError) as e:
         lsh.load_index(fam2, tmp_path / "missing.bin")
     assert e.value.status == 8  # LSH_EIO
