@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   float4 *consts = reinterpret_cast<float4 *>(smem + KMAX * TILE_A + SB * TILE_B);  // [epi warp][CONST_Q][8]
   __shared__ __align__(8) uint64_t afull[KMAX], aempty[KMAX], bfull[SB], bempty[SB], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
-  __shared__ uint2 kpart[BM][2];  // M = 64: the upper slice's partial keys
+  __shared__ uint2 kpart[BM][3];  // M = 64: the odd slices' partial keys; M = 128: slices 1..3
   __shared__ volatile int aborted;  // set on a timed-out wait: later waits are skipped
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int ntn = int(a.ML / BN);
@@ -797,6 +797,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
       }
+      if (M == 128) {
+        // E2LSH only: one table spans the four slices; slices 1..3 hand their
+        // partial sums to slice 0 (the key is a sum mod 2^32 in each half)
+        static_assert(M != 128 || !SRP, "m = 128 on the tensor cores is E2LSH only");
+        const int r = q * 32 + lane;
+        if (slice != 0) kpart[r][slice - 1] = make_uint2(ha, hb);
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+        if (slice == 0 && valid && a.keys) {
+          const uint2 o1 = kpart[r][0], o2 = kpart[r][1], o3 = kpart[r][2];
+          const uint64_t key = (uint64_t(ha + o1.x + o2.x + o3.x) << 32) | (hb + o1.y + o2.y + o3.y);
+          a.keys[int64_t(n0 / 128) * a.key_ld + row] = bad ? ~0ull : key;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+      }
     }
     if (nbad) {
       if (a.counters) atomicAdd(a.counters + CNT_NONFINITE, (unsigned long long)nbad);
@@ -1026,7 +1040,8 @@ bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X) {
     return false;
   const int per = fp8 ? 16 : 8;  // elements per 16 bytes (TMA rows and strides)
   if (fd.d % per != 0 || X->ld % per != 0 || (reinterpret_cast<uintptr_t>(X->values) & 15) != 0) return false;
-  if (ML % BN != 0 || 64 % fd.m != 0) return false;  // a 32-column slice or a pair of them holds whole tables
+  // a 32-column slice, a pair of them, or (E2LSH, m = 128) the whole 128-column tile holds whole tables
+  if (ML % BN != 0 || (64 % fd.m != 0 && !(fd.m == 128 && fd.kind == LSH_E2LSH))) return false;
   if (fp8 && fd.m < 8) return false;
   if (fd.d > 16384) return false;  // larger rows stream their K slices; bounded for the scratch records
   if (X->n > (int64_t(1) << 31) - BM || (X->n + BM - 1) / BM > 2147483647) return false;
@@ -1097,6 +1112,7 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float 
   case 2 * M + 1: kern = tc_dense_kernel<true, M, false>; break;
       LSH_TC_CASE(1) LSH_TC_CASE(2) LSH_TC_CASE(4) LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
 #undef LSH_TC_CASE
+      case 2 * 128: kern = tc_dense_kernel<false, 128, false>; break;
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -1106,6 +1122,7 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float 
   case 2 * M + 1: kern = tc_dense_kernel<true, M, true>; break;
       LSH_TC_CASE(8) LSH_TC_CASE(16) LSH_TC_CASE(32) LSH_TC_CASE(64)
 #undef LSH_TC_CASE
+      case 2 * 128: kern = tc_dense_kernel<false, 128, true>; break;
       default: return cudaErrorInvalidValue;
     }
   }

@@ -257,3 +257,15 @@ def test_dense_tensor_core_full_size_sampled(compute):
     fam.close()
     del X, out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,d,L", [(700, 256, 3), (300, 960, 2), (9000, 512, 1)])
+def test_dense_tensor_core_m128(n, d, L):
+    """E2LSH with m = 128 on the tensor cores: one table fills a 128-column
+    tile and its four 32-column slices combine their partial keys; BF16 and
+    per-row-scaled FP8 rows against the oracle (9,000 rows: queued rechecks)."""
+    X = workloads.iid(n, d, seed=n + d + 1, device="cpu", dtype=torch.bfloat16).cuda()
+    stats, _ = compare_hash(dict(kind="e2lsh", d=d, m=128, L=L, w=4.0, seed=33, compute=1), X)
+    assert stats["n_changed"] <= stats["n_flagged"]
+    st = _fp8_compare("e2lsh", n, d, 128, L, seed=n + d + 2)
+    assert st["n_changed"] <= st["n_flagged"]
