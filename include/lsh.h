@@ -254,22 +254,73 @@ lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t
 /*
  * Pin the tile plan of the dense-row CS/HCS hashing kernel for every later
  * call in this process (any family, any device), in place of the autotuned
- * one; all five arguments 0 restore the automatic choice.  Every plan
+ * one; all six arguments 0 restore the automatic choice.  Every plan
  * computes the same codes and keys; the plan only sets how the work maps to
  * the GPU:
  *   rows_per_lane    1, 2 or 4 rows per thread (one vector shared-memory load
  *                    per term serves them all);
- *   row_groups       1, 2 or 4 groups of 32 lanes per row tile, with
- *                    rows_per_lane * row_groups <= 4;
+ *   row_groups       1, 2 or 4 row groups per tile: groups of 32 lanes, or
+ *                    of 16 with split_bins; a tile holds at most 128 rows;
  *   warps_per_table  1, 2 or 4 warps sharing the bins of one table;
  *   tables_per_cta   >= 1, the largest table group a CTA stages (balanced);
- *   entry_bytes      2 or 4, the width of a member-list entry.
+ *   entry_bytes      2 or 4, the width of a member-list entry;
+ *   split_bins       0, or 1: the two halves of a warp sum alternate quads
+ *                    of every bin for the same 16 lanes' rows and combine
+ *                    their sums at the end of the bin (rows_per_lane >= 2),
+ *                    which keeps rows_per_lane rows per thread in a tile of
+ *                    half the rows.
  * Host only; returns LSH_EINVAL for values outside these sets.  A pinned plan
  * whose shared memory does not fit a shape (or 2-byte entries for
- * d * rows_per_lane * 4 > 65535) makes lsh_hash return LSH_EUNSUPPORTED.
+ * d * rows_per_lane * 4 > 16383) makes lsh_hash return LSH_EUNSUPPORTED.
  */
 lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_t warps_per_table,
-                               int32_t tables_per_cta, int32_t entry_bytes);
+                               int32_t tables_per_cta, int32_t entry_bytes, int32_t split_bins);
+
+/*
+ * The tile plan a dense-row CS/HCS hash of n rows of dtype would use now: the
+ * pinned plan, else the one the autotuner chose for the shape (after a call
+ * of 131,072 rows or more), else the default.  plan[6] receives
+ * rows_per_lane, row_groups, warps_per_table, tables_per_cta (the balanced
+ * group size actually staged), entry_bytes and split_bins.  Host only (no
+ * timing, no device work); LSH_EUNSUPPORTED for dense families or when no
+ * plan fits the shape.
+ */
+lsh_status lsh_get_sketch_plan(lsh_family_t fam, int32_t dtype, int64_t n, int32_t plan[6]);
+
+/*
+ * Replayed hashing of uneven batches of dense rows (keys only; the m*L hashes
+ * of Definitions 12, 19, 25, 31 and the bucket keys of Sec. 3.1, equal to
+ * lsh_hash's bit for bit).  A hasher captures, per batch-size bucket (powers
+ * of two from 8,192 rows up to max_rows), one CUDA graph of the hashing --
+ * recheck-queue reset, the sketch kernel over all L tables, the exact recheck
+ * of the queued bins (batches of up to 8,192 rows recheck in place, in the
+ * sketch kernel) -- sized for the bucket's largest batch, and replays it
+ * for every batch that falls in the bucket; only a device-side batch
+ * descriptor (X, n, keys, key_ld), written by the graph's first node,
+ * changes between replays.  The first batch of a bucket captures its graph
+ * (after the autotuner has timed the shape on that batch, when it has
+ * 131,072 rows or more; a plan pinned with lsh_set_sketch_plan at capture
+ * time is kept).
+ *   fam       a CS-E2LSH, HCS-E2LSH, CS-SRP, HCS-SRP or CSSRP-L family whose
+ *             rows fit the dense-row kernel's tile (borrowed: it must outlive
+ *             the hasher); dense families return LSH_EUNSUPPORTED
+ *   dtype     LSH_F32, LSH_BF16 or LSH_F16; ld the row stride in elements
+ *             (>= d) of every batch
+ *   max_rows  the largest batch (1 <= max_rows < 2^32 - 1); the hasher holds
+ *             a recheck queue for it (16 B per 256 of max_rows*L*m, rounded up
+ *             to a power of two rows, plus 1 MiB)
+ * lsh_hasher_run hashes the n rows at device pointer X (16-byte aligned when
+ * ld times the element size is a multiple of 16) into keys [L][key_ld]
+ * (key_ld >= n), stream-ordered; 0 <= n <= max_rows.  Calls on one hasher
+ * must be ordered on one stream (they share the descriptor and the queue).
+ * lsh_hasher_info reports the graphs captured and the replays launched.
+ * lsh_hasher_destroy waits for the device, then frees the graphs.
+ */
+typedef struct lsh_hasher_s *lsh_hasher_t;
+lsh_status lsh_hasher_create(lsh_family_t fam, int32_t dtype, int64_t ld, int64_t max_rows, lsh_hasher_t *out);
+lsh_status lsh_hasher_run(lsh_hasher_t h, const void *X, int64_t n, uint64_t *keys, int64_t key_ld, void *stream);
+lsh_status lsh_hasher_info(lsh_hasher_t h, int64_t *captures, int64_t *replays);
+void lsh_hasher_destroy(lsh_hasher_t h);
 
 /*
  * Build the L hash tables of Sec. 3.1 over X: hash (keys only), then per

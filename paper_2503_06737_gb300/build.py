@@ -59,7 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cuda = _cuda_home()
     os.makedirs(OBJ, exist_ok=True)
     nvcc, jobs = _cmds(cuda)
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               glob.glob(os.path.join(INCLUDE, "*.h")))
     todo = [(s, o, c) for s, o, c in jobs if force or _stale(o, [s, *headers])]
 
     def run(job):

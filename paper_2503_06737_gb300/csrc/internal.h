@@ -118,6 +118,15 @@ namespace lsh {
 // ---------------------------------------------------------------------------
 // Kernel launchers (each returns cudaSuccess or the launch error).
 // ---------------------------------------------------------------------------
+// The batch of a replayed hashing graph (lsh_hasher): written on the device
+// by the graph's first node, read by the kernels after it.
+struct BatchDesc {
+  const void *X;
+  int64_t n;
+  uint64_t *keys;
+  int64_t key_ld;
+};
+
 struct SketchLaunch {
   // input
   const void *X;
@@ -149,6 +158,10 @@ struct SketchLaunch {
   int4 *queue = nullptr;
   uint32_t *qcount = nullptr;
   uint32_t qcap = 0;
+  // replayed batches (dense-row sketch kernels only): X, n, keys and key_ld
+  // come from this device descriptor at run time; the fields above then give
+  // the largest batch the launch is sized for
+  const BatchDesc *desc = nullptr;
 };
 
 // Dense-row CS/HCS hashing (all L tables, one launch).  With p.queue set,
@@ -163,7 +176,7 @@ int64_t sketch_queue_cap(int64_t n, int32_t L, int32_t m);
 struct SketchPlan { int tables_per_cta, groups, row_groups, warps, smem, ctas; bool ok; };
 SketchPlan plan_sketch_dense(int d, int m, int L, int cap, int dtype);
 // Process-wide pinned plan of the dense-row kernel (all zeros: autotuned).
-struct SketchPin { int rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes; };
+struct SketchPin { int rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes, split_bins; };
 void set_sketch_pin(const SketchPin &pin);
 // False when a pinned plan does not fit the shape (the call must not launch).
 bool sketch_pin_fits(int d, int m, int L, int cap);
@@ -174,6 +187,19 @@ bool sketch_pin_fits(int d, int m, int L, int cap);
 // dense-row kernel's tile -- bounded per bin with the member counts of mseg.
 cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, const int32_t *col, const float *val,
                               const uint16_t *colmajor, const uint32_t *mseg, cudaStream_t stream);
+
+// The family fields of a launch (tables, offsets, key multipliers, w).
+SketchLaunch family_launch(const lsh_family_s *f);
+
+// Time the dense-row kernel's candidate plans for the shape of p on its first
+// rows (once per shape; nothing when a plan is pinned, the shape is cached,
+// or p has fewer rows than the tuner needs), so that a later launch -- or a
+// stream capture, which cannot time -- finds the tuned plan.
+void sketch_autotune(const SketchLaunch &p, cudaStream_t stream);
+// The plan a launch of p would use now (pinned, else tuned for the shape,
+// else the default); tables_per_cta is the balanced group size.  False when
+// no plan fits.
+bool sketch_current_plan(const SketchLaunch &p, SketchPin &out);
 
 // Hash the rows of X into keys [L][key_ld] (+ optional codes, proj, counters);
 // stream-ordered, allocates nothing when counters is NULL.

@@ -119,22 +119,9 @@ size_t dtype_size(int dt) { return dt == LSH_F32 ? 4 : (dt == LSH_FP8_E4M3 ? 1 :
 
 }  // namespace
 
-// Hash into keys [L][key_ld] (and the optional outputs).  Stream-ordered.
-lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
-                     float *proj, unsigned long long *counters, cudaStream_t stream) {
+SketchLaunch family_launch(const lsh_family_s *f) {
   const lsh_family_desc &d = f->host.desc;
-  if (X->n == 0) return LSH_OK;
-  if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
-  if (X->dtype == LSH_FP8_E4M3 && !(f->d_Gt8 && tc_dense_supported(d, X)))
-    return fail(LSH_EUNSUPPORTED, "FP8 rows are hashed by dense families with an FP8 G on the tensor cores "
-                                  "(d <= 16384 and the row stride multiples of 16, m in 8..64 dividing 64 or E2LSH with m = 128, "
-                                  "m*L a multiple of 128)");
   SketchLaunch p{};
-  p.X = X->values;
-  p.row_scale = X->row_scale;
-  p.dtype = X->dtype;
-  p.n = X->n;
-  p.ld = X->ld;
   p.d = d.d;
   p.kind = d.kind;
   p.m = d.m;
@@ -155,6 +142,26 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
   p.kb = f->d_kb;
   p.w = d.w;
   p.sqrtm = kind_scaled(d.kind) ? std::sqrt(double(d.m)) : 1.0;
+  p.status = f->d_status;
+  return p;
+}
+
+// Hash into keys [L][key_ld] (and the optional outputs).  Stream-ordered.
+lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t *keys, int64_t key_ld,
+                     float *proj, unsigned long long *counters, cudaStream_t stream) {
+  const lsh_family_desc &d = f->host.desc;
+  if (X->n == 0) return LSH_OK;
+  if (kind_is_dense(d.kind) && X->rowptr) return fail(LSH_EUNSUPPORTED, "dense E2LSH/SRP takes dense rows");
+  if (X->dtype == LSH_FP8_E4M3 && !(f->d_Gt8 && tc_dense_supported(d, X)))
+    return fail(LSH_EUNSUPPORTED, "FP8 rows are hashed by dense families with an FP8 G on the tensor cores "
+                                  "(d <= 16384 and the row stride multiples of 16, m in 8..64 dividing 64 or E2LSH with m = 128, "
+                                  "m*L a multiple of 128)");
+  SketchLaunch p = family_launch(f);
+  p.X = X->values;
+  p.row_scale = X->row_scale;
+  p.dtype = X->dtype;
+  p.n = X->n;
+  p.ld = X->ld;
   if (kind_is_srp(d.kind))
     p.bits = static_cast<uint64_t *>(codes);
   else
@@ -594,18 +601,40 @@ lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t
 }
 
 lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_t warps_per_table,
-                               int32_t tables_per_cta, int32_t entry_bytes) {
+                               int32_t tables_per_cta, int32_t entry_bytes, int32_t split_bins) {
   const bool clear = rows_per_lane == 0 && row_groups == 0 && warps_per_table == 0 && tables_per_cta == 0 &&
-                     entry_bytes == 0;
+                     entry_bytes == 0 && split_bins == 0;
   if (!clear) {
     auto in124 = [](int v) { return v == 1 || v == 2 || v == 4; };
-    if (!in124(rows_per_lane) || !in124(row_groups) || rows_per_lane * row_groups > 4)
-      return fail(LSH_EINVAL, "rows_per_lane and row_groups must be 1, 2 or 4 with a product <= 4");
+    if (split_bins != 0 && split_bins != 1) return fail(LSH_EINVAL, "split_bins must be 0 or 1");
+    if (!in124(rows_per_lane) || !in124(row_groups))
+      return fail(LSH_EINVAL, "rows_per_lane and row_groups must be 1, 2 or 4");
+    if (split_bins ? (rows_per_lane < 2 || rows_per_lane * row_groups > 8) : rows_per_lane * row_groups > 4)
+      return fail(LSH_EINVAL, "a tile holds at most 128 rows (split bins: 16 row groups per warp and "
+                              "rows_per_lane >= 2)");
     if (!in124(warps_per_table)) return fail(LSH_EINVAL, "warps_per_table must be 1, 2 or 4");
     if (tables_per_cta < 1) return fail(LSH_EINVAL, "tables_per_cta must be >= 1");
     if (entry_bytes != 2 && entry_bytes != 4) return fail(LSH_EINVAL, "entry_bytes must be 2 or 4");
   }
-  set_sketch_pin(SketchPin{rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes});
+  set_sketch_pin(SketchPin{rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes, split_bins});
+  return LSH_OK;
+}
+
+lsh_status lsh_get_sketch_plan(lsh_family_t fam, int32_t dtype, int64_t n, int32_t plan[6]) {
+  if (!fam || !plan) return fail(LSH_EINVAL, "lsh_get_sketch_plan: NULL argument");
+  const lsh_family_desc &d = fam->host.desc;
+  if (kind_is_dense(d.kind)) return fail(LSH_EUNSUPPORTED, "lsh_get_sketch_plan: CS/HCS families only");
+  if (dtype != LSH_F32 && dtype != LSH_BF16 && dtype != LSH_F16) return fail(LSH_EINVAL, "unknown dtype");
+  if (n < 1) return fail(LSH_EINVAL, "lsh_get_sketch_plan: n must be >= 1");
+  SketchLaunch p = family_launch(fam);
+  p.dtype = dtype;
+  p.n = n;
+  p.ld = d.d;
+  SketchPin pin;
+  if (!sketch_current_plan(p, pin)) return fail(LSH_EUNSUPPORTED, "no sketch plan fits this shape");
+  const int32_t v[6] = {pin.rows_per_lane, pin.row_groups, pin.warps_per_table, pin.tables_per_cta,
+                        pin.entry_bytes, pin.split_bins};
+  for (int i = 0; i < 6; ++i) plan[i] = v[i];
   return LSH_OK;
 }
 

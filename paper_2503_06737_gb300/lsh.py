@@ -96,7 +96,8 @@ SIGNATURES = [
     ("lsh_family_status", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     ("lsh_family_destroy", None, [P]),
     ("lsh_hash", ctypes.c_int, [P, ctypes.POINTER(Matrix), P, P, P, ctypes.POINTER(HashStats), P]),
-    ("lsh_set_sketch_plan", ctypes.c_int, [ctypes.c_int32] * 5),
+    ("lsh_set_sketch_plan", ctypes.c_int, [ctypes.c_int32] * 6),
+    ("lsh_get_sketch_plan", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P]),
     ("lsh_build_index", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, ctypes.POINTER(P), P]),
     ("lsh_index_rebuild", ctypes.c_int, [P, ctypes.POINTER(Matrix), P]),
     ("lsh_index_rebuild_host", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int64, P]),
@@ -110,6 +111,10 @@ SIGNATURES = [
     ("lsh_merge_topk", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P),
                                       ctypes.POINTER(P), P, P, P]),
     ("lsh_build_tables_static", ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P]),
+    ("lsh_hasher_create", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(P)]),
+    ("lsh_hasher_run", ctypes.c_int, [P, P, ctypes.c_int64, P, ctypes.c_int64, P]),
+    ("lsh_hasher_info", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("lsh_hasher_destroy", None, [P]),
     ("lsh_server_create", ctypes.c_int, [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
     ("lsh_server_submit", ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     ("lsh_server_wait", ctypes.c_int, [P, ctypes.c_int64, P, P, ctypes.POINTER(ctypes.c_double)]),
@@ -138,9 +143,11 @@ def launch_count() -> int:
     return int(lib().lsh_launch_count())
 
 
-def set_sketch_plan(rows_per_lane=0, row_groups=0, warps_per_table=0, tables_per_cta=0, entry_bytes=0):
+def set_sketch_plan(rows_per_lane=0, row_groups=0, warps_per_table=0, tables_per_cta=0, entry_bytes=0,
+                    split_bins=0):
     """Pin the dense-row sketch kernel's plan process-wide (all zeros: autotuned)."""
-    _check(lib().lsh_set_sketch_plan(rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes))
+    _check(lib().lsh_set_sketch_plan(rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes,
+                                     split_bins))
 
 
 def _check(st: int):
@@ -252,6 +259,14 @@ class Family:
         _check(lib().lsh_family_export(self.handle, p(bins), p(signs), p(G), p(b), p(ka), p(kb)))
         return dict(bins=bins, signs=signs, G=G, b=b, ka=ka, kb=kb)
 
+    def sketch_plan(self, n, dtype=torch.float32) -> dict:
+        """The tile plan a dense-row hash of n rows would use now (pinned, tuned or default)."""
+        import numpy as np
+        v = np.zeros(6, np.int32)
+        _check(lib().lsh_get_sketch_plan(self.handle, _TORCH_DTYPE[dtype], int(n), ctypes.c_void_p(v.ctypes.data)))
+        keys = ("rows_per_lane", "row_groups", "warps_per_table", "tables_per_cta", "entry_bytes", "split_bins")
+        return dict(zip(keys, (int(x) for x in v)))
+
     def status(self, clear=True) -> int:
         s = ctypes.c_int32()
         _check(lib().lsh_family_status(self.handle, ctypes.byref(s), int(clear)))
@@ -300,6 +315,46 @@ class Family:
     def close(self):
         if getattr(self, "handle", None):
             lib().lsh_family_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hasher:
+    """Replayed hashing of uneven batches (keys only): one captured CUDA graph
+    per batch-size bucket, replayed with the batch's pointer and row count."""
+
+    def __init__(self, family: "Family", dtype=torch.float32, ld=None, max_rows=1 << 20):
+        self.family = family
+        self.dtype = dtype
+        self.ld = int(ld if ld is not None else family.d)
+        h = ctypes.c_void_p()
+        _check(lib().lsh_hasher_create(family.handle, _TORCH_DTYPE[dtype], self.ld, int(max_rows), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, X: torch.Tensor, keys: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Keys [L, n] of the rows of X [n, d] (row stride ld); into keys if given ([L, >= n], int64)."""
+        n = int(X.shape[0])
+        if X.dtype != self.dtype or X.shape[1] != self.family.d or (n > 1 and X.stride(0) != self.ld) \
+                or X.stride(1) != 1:
+            raise ValueError("X must match the hasher's dtype, d and row stride")
+        if keys is None:
+            keys = torch.empty((self.family.L, n), dtype=torch.int64, device=X.device)
+        _check(lib().lsh_hasher_run(self.handle, _ptr(X), n, _ptr(keys), int(keys.stride(0)), _stream(stream)))
+        return keys
+
+    def info(self):
+        c, r = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().lsh_hasher_info(self.handle, ctypes.byref(c), ctypes.byref(r)))
+        return dict(captures=int(c.value), replays=int(r.value))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().lsh_hasher_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -107,12 +107,14 @@ def test_sketch_plan_pin_validation(L):
     """The plan pin is host-only: out-of-set values are refused, valid ones and
     the all-zero reset are accepted (no device needed)."""
     lib = L.lib()
-    for args in [(3, 1, 1, 1, 2), (4, 2, 1, 1, 2), (1, 1, 3, 1, 2), (1, 1, 1, 0, 2), (1, 1, 1, 4, 3),
-                 (0, 1, 1, 1, 2)]:
+    for args in [(3, 1, 1, 1, 2, 0), (4, 2, 1, 1, 2, 0), (1, 1, 3, 1, 2, 0), (1, 1, 1, 0, 2, 0),
+                 (1, 1, 1, 4, 3, 0), (0, 1, 1, 1, 2, 0), (1, 1, 1, 1, 2, 1), (4, 4, 1, 1, 2, 1),
+                 (2, 1, 1, 1, 2, 2)]:
         assert lib.lsh_set_sketch_plan(*args) == 1, args  # LSH_EINVAL
-    for args in [(1, 4, 2, 25, 2), (4, 1, 1, 8, 4), (2, 2, 4, 1, 4)]:
+    for args in [(1, 4, 2, 25, 2, 0), (4, 1, 1, 8, 4, 0), (2, 2, 4, 1, 4, 0), (2, 1, 2, 8, 2, 1),
+                 (4, 2, 1, 3, 4, 1), (2, 4, 4, 1, 2, 1)]:
         assert lib.lsh_set_sketch_plan(*args) == 0, args
-    assert lib.lsh_set_sketch_plan(0, 0, 0, 0, 0) == 0
+    assert lib.lsh_set_sketch_plan(0, 0, 0, 0, 0, 0) == 0
 
 
 def test_merge_topk_against_restatement(L):

@@ -237,8 +237,10 @@ def test_deferred_recheck_queue_overflow():
 # Every plan of the dense-row kernel computes the same codes: pin each shape
 # (rows per lane, row groups, warps per table, tables per CTA, entry bytes)
 # and check the keys-only and the full instantiations against the oracle.
-PLANS = [(1, 1, 1, 4, 2), (1, 1, 2, 50, 4), (1, 2, 4, 8, 2), (1, 4, 1, 3, 4), (2, 1, 2, 6, 2),
-         (2, 1, 1, 16, 4), (2, 2, 1, 5, 2), (4, 1, 2, 4, 2), (4, 1, 4, 2, 4), (4, 1, 1, 32, 2)]
+PLANS = [(1, 1, 1, 4, 2, 0), (1, 1, 2, 50, 4, 0), (1, 2, 4, 8, 2, 0), (1, 4, 1, 3, 4, 0), (2, 1, 2, 6, 2, 0),
+         (2, 1, 1, 16, 4, 0), (2, 2, 1, 5, 2, 0), (4, 1, 2, 4, 2, 0), (4, 1, 4, 2, 4, 0), (4, 1, 1, 32, 2, 0),
+         (2, 1, 2, 8, 2, 1), (2, 1, 1, 50, 4, 1), (2, 2, 4, 3, 2, 1), (4, 1, 2, 6, 2, 1), (4, 2, 1, 4, 4, 1),
+         (2, 4, 2, 2, 2, 1)]
 PLAN_SHAPES = [
     # kind, d, m, L, dims, mdims, dtype
     ("cs_e2lsh", 960, 64, 13, None, None, torch.float32),
@@ -298,3 +300,19 @@ def test_hash_csl_srp(d, m, l, L, n, dtype):
     if d == 960:
         for plan in PLANS:
             _pinned(plan, lambda: compare_keys_only(fa, X))
+
+
+def test_sketch_plan_query():
+    """lsh_get_sketch_plan reports the pinned plan (with the balanced table
+    group actually staged) and, unpinned, the default plan of a small batch."""
+    fam = lsh.Family("cs_e2lsh", 960, 64, 13, w=4.0, seed=31)
+    lsh.set_sketch_plan(2, 1, 2, 8, 2, 1)
+    try:
+        assert fam.sketch_plan(5000) == dict(rows_per_lane=2, row_groups=1, warps_per_table=2, tables_per_cta=7,
+                                             entry_bytes=2, split_bins=1)
+    finally:
+        lsh.set_sketch_plan()
+    p = fam.sketch_plan(5000)
+    assert p["rows_per_lane"] * p["row_groups"] * (16 if p["split_bins"] else 32) == 32  # one 32-row tile
+    assert p["tables_per_cta"] >= 1 and p["entry_bytes"] in (2, 4)
+    fam.close()
