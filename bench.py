@@ -377,6 +377,55 @@ def extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream):
     return out
 
 
+def uneven_batches(X, keys, e0, e1, stream, batches=200, seed=11):
+    """Uneven hashing batches (row counts log-uniform in two ranges), keys
+    only, CS-E2LSH m = 64, L = 50 on the headline rows: one lsh_hash call per
+    batch against one lsh_hasher replay per batch (a captured CUDA graph per
+    power-of-two size bucket).  Device time (CUDA events around the whole
+    sequence) and host wall time per batch."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2503_06737_gb300 import lsh
+    d = X.shape[1]
+    fam = lsh.Family("cs_e2lsh", d, 64, 50, w=4.0, seed=42)
+    key_ld = keys.shape[1]
+    rng = np.random.default_rng(seed)
+    out = {"family": "cs_e2lsh m=64 L=50", "batches": batches}
+    for lo, hi in ((64, 8192), (8192, 131072)):
+        sizes = [int(math.exp(rng.uniform(math.log(lo), math.log(hi)))) for _ in range(batches)]
+        mtx = [lsh.dense_matrix(X[:n]) for n in sizes]
+        h = lsh.Hasher(fam, dtype=X.dtype, max_rows=hi)
+        xp, kp = lsh._ptr(X), lsh._ptr(keys)
+        st = lsh._stream(stream)
+
+        def direct():
+            for mt in mtx:
+                fam.hash_into(mt, None, kp, None, stream=stream)
+
+        def replay():
+            for nb in sizes:
+                lsh._check(lsh.lib().lsh_hasher_run(h.handle, xp, nb, kp, key_ld, st))
+
+        row = {"rows": int(sum(sizes))}
+        for name, fn in (("lsh_hash", direct), ("hasher_graphs", replay)):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            row[name] = {"device_ms": e0.elapsed_time(e1), "wall_ms": wall * 1e3,
+                         "us_per_batch": wall * 1e6 / batches, "points_per_s": row["rows"] / wall}
+        row["hasher_info"] = h.info()
+        out[f"rows_{lo}_{hi}"] = row
+        h.close()
+    fam.close()
+    return out
+
+
 def precision_sweep(peaks, alu_peak, e0, e1, stream, dev):
     """4,000,000 x 512 BF16 rows, m = 32, L = 64: dense E2LSH on the tensor cores
     (GEMM 4M x 512 x 2048, BF16 family, and per-row-scaled FP8 rows with an E4M3
@@ -759,6 +808,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "kernel": "sketch_dense_kernel (CS/HCS hash, all tables, keys only)",
+                "plan": fam.sketch_plan(n, X.dtype),
                 "kernel_ms": hash_ms, "peak_source": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
                 "hbm_view": {"algorithmic_bytes": bytes_alg,
                              "achieved_gbs": bytes_alg / (hash_ms / 1e3) / 1e9,
@@ -823,7 +873,26 @@ def main():
                               "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
                               "changed": st["n_changed"]}
             f2.close()
+        # CSSRP-L (Table 1): l bins per coordinate, l times the count sketch's adds
+        for lc in (2, 4):
+            fa = dict(_workload(args.workload, "cs_srp")[1], kind="csl_srp", l=lc)
+            f2 = lsh.Family(**fa)
+            for _ in range(3):
+                f2.hash_into(mtx, None, lsh._ptr(keys), None)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                f2.hash_into(mtx, None, lsh._ptr(keys), None)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kms = e0.elapsed_time(e1) / 10
+            variants[f"csl_srp_l{lc}"] = {"hash_ms": kms, "points_per_s": n / (kms / 1e3),
+                                          "alu_frac": lc * adds / (kms / 1e3) / 1e12 / alu_peak,
+                                          "note": f"CSSRP-L, {lc} nonzeros per column of the sketch matrix"}
+            f2.close()
         log("per-family hashing done")
+        variants["uneven_batches_gmm64_d960"] = uneven_batches(X, keys, e0, e1, stream)
+        log("uneven batches done")
         variants.update(extra_variants(args, X, keys, peaks, alu_peak, e0, e1, stream))
         log("extra variants done")
         del keys
