@@ -239,8 +239,8 @@ void lsh_family_destroy(lsh_family_t fam);
  * Rows that hold NaN/Inf get key 0xFFFFFFFFFFFFFFFF and code INT32_MIN.
  * Stream-ordered and asynchronous, with two exceptions: the first dense-row
  * CS/HCS call of a shape (device, kind, d, m, L, modes, dtype) with at least
- * 131,072 rows times the candidate tile plans of the hashing kernel on its
- * first 131,072 rows and waits for them (once per shape; skipped while the
+ * 524,288 rows times the candidate tile plans of the hashing kernel on its
+ * first 524,288 rows and waits for them (once per shape; skipped while the
  * stream is captured); and calls with stats synchronise.  Temporaries come
  * from the device's stream-ordered memory pool: the recheck queue of a
  * dense-row CS/HCS batch of 8,192 rows or more (16 B per 256 entries of
@@ -279,7 +279,7 @@ lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_
 /*
  * The tile plan a dense-row CS/HCS hash of n rows of dtype would use now: the
  * pinned plan, else the one the autotuner chose for the shape (after a call
- * of 131,072 rows or more), else the default.  plan[6] receives
+ * of 524,288 rows or more), else the default.  plan[6] receives
  * rows_per_lane, row_groups, warps_per_table, tables_per_cta (the balanced
  * group size actually staged), entry_bytes and split_bins.  Host only (no
  * timing, no device work); LSH_EUNSUPPORTED for dense families or when no
@@ -299,7 +299,7 @@ lsh_status lsh_get_sketch_plan(lsh_family_t fam, int32_t dtype, int64_t n, int32
  * descriptor (X, n, keys, key_ld), written by the graph's first node,
  * changes between replays.  The first batch of a bucket captures its graph
  * (after the autotuner has timed the shape on that batch, when it has
- * 131,072 rows or more; a plan pinned with lsh_set_sketch_plan at capture
+ * 524,288 rows or more; a plan pinned with lsh_set_sketch_plan at capture
  * time is kept).
  *   fam       a CS-E2LSH, HCS-E2LSH, CS-SRP, HCS-SRP or CSSRP-L family whose
  *             rows fit the dense-row kernel's tile (borrowed: it must outlive

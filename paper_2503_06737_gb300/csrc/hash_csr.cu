@@ -449,12 +449,40 @@ __global__ void __launch_bounds__(256, 2) sketch_csr_kernel(const __grid_constan
     for (int tb = 0; tb < L; tb += TB) {
       const int nt = min(TB, L - tb);
       // ---- scatter: one shared atomic per (nonzero, table) ----
-      if (rowok) {
+      if (rowok && vec4) {
+        // count sketch from global memory: the entry loads of all the lane's
+        // buffered nonzeros (four tables per 8-byte load) in flight before
+        // their atomics
+        constexpr int kBatch = kReg / 2;
+        for (int g = 0; g < nt; g += 4) {
+#pragma unroll
+          for (int k0 = 0; k0 < kReg; k0 += kBatch) {
+            uint2 q[kBatch];
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k)
+              if (k0 + k < kn)
+                q[k] = __ldg(reinterpret_cast<const uint2 *>(a.colmajor + int64_t(nz[(k0 + k) * kWarp + lane].y) * L +
+                                                             tb + g));
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+              if (k0 + k < kn) {
+                const float x = __uint_as_float(nz[(k0 + k) * kWarp + lane].x);
+                const uint32_t e[4] = {q[k].x & 0xffffu, q[k].x >> 16, q[k].y & 0xffffu, q[k].y >> 16};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  atomicAdd(&acc[(g + i) * m + int(e[i] & 0x7fffu)], (e[i] >> 15) ? -x : x);
+              }
+            }
+          }
+        }
+      } else if (rowok) {
 #pragma unroll 1
         for (int k = 0; k < kn; ++k) {
           const uint2 z = nz[k * kWarp + lane];
           scatter_one(a, tab, acc, tb, nt, vec4, z.y, __uint_as_float(z.x));
         }
+      }
+      if (rowok) {
         for (int64_t e = rs + kWarp * kReg + lane; e < re; e += kWarp)
           scatter_one(a, tab, acc, tb, nt, vec4, prep_state(a, nz_col<SRC>(a, e)), nz_val<SRC>(a, xrow, e));
       }

@@ -212,7 +212,7 @@ cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stre
 // which the real launch then overwrites -- and keeps the fastest.  It is
 // skipped while the stream is being captured (the default plan is used).
 // Every plan computes the same codes, and a plan fits any row count.
-constexpr int64_t kTuneRows = 131072;
+constexpr int64_t kTuneRows = 524288;  // enough tiles per CTA that the tail of the last wave is small
 
 struct TuneKey {
   int dev, kind, d, m, L, N, dtype, cap;

@@ -229,23 +229,67 @@ __device__ __forceinline__ void sts_x(uint32_t a, const float (&v)[RPL]) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
   }
 }
-// One quad of entries: the four offsets (flags masked off) and the raw
-// first word (whose first entry carries the flags).
-template <typename EntT>
-__device__ __forceinline__ void lds_quad_raw(uint32_t qaddr, uint32_t (&o)[4], uint32_t &w0) {
-  if constexpr (sizeof(EntT) == 2) {
-    uint32_t x, y;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(qaddr));
-    w0 = x;
-    o[0] = x & EntFlags<EntT>::kMask;
-    o[1] = x >> 16;
-    o[2] = y & 0xFFFFu;
-    o[3] = y >> 16;
+// Packed FP32 pairs: the x_j of two rows of a lane (adjacent words) and
+// their accumulators travel as one 64-bit register pair, so that one
+// fma.rn.f32x2 -- two independent IEEE single-precision fmas -- adds a term
+// to both rows.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+template <int NP>
+__device__ __forceinline__ void lds_x2(uint32_t a, uint64_t (&v)[NP]) {
+  if constexpr (NP == 1) {
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v[0]) : "r"(a));
   } else {
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3])
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(v[0]), "=l"(v[1]) : "r"(a));
+  }
+}
+
+// One quad of entries as stored (two words of 16-bit entries, four of
+// 32-bit ones), and its decoding: the four offsets (flags masked off) and the
+// raw first word (whose first entry carries the flags).
+template <typename EntT>
+struct QuadWords;
+template <>
+struct QuadWords<uint16_t> {
+  uint32_t w[2];
+};
+template <>
+struct QuadWords<uint32_t> {
+  uint32_t w[4];
+};
+template <typename EntT>
+__device__ __forceinline__ void lds_quad_words(uint32_t qaddr, QuadWords<EntT> &q) {
+  if constexpr (sizeof(EntT) == 2) {
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(q.w[0]), "=r"(q.w[1]) : "r"(qaddr));
+  } else {
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q.w[0]), "=r"(q.w[1]), "=r"(q.w[2]), "=r"(q.w[3])
                  : "r"(qaddr));
-    w0 = o[0];
-    o[0] &= EntFlags<EntT>::kMask;
+  }
+}
+template <typename EntT>
+__device__ __forceinline__ void decode_quad(const QuadWords<EntT> &q, uint32_t (&o)[4], uint32_t &w0) {
+  w0 = q.w[0];
+  if constexpr (sizeof(EntT) == 2) {
+    o[0] = q.w[0] & EntFlags<EntT>::kMask;
+    o[1] = q.w[0] >> 16;
+    o[2] = q.w[1] & 0xFFFFu;
+    o[3] = q.w[1] >> 16;
+  } else {
+    o[0] = q.w[0] & EntFlags<EntT>::kMask;
+    o[1] = q.w[1];
+    o[2] = q.w[2];
+    o[3] = q.w[3];
   }
 }
 
@@ -674,17 +718,35 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
       // epilogue
       const uint2 rb = rng[tl * (kMaxWpt + 1) + sub], rn = rng[tl * (kMaxWpt + 1) + sub + 1];
       int l = int(rb.x);
+      // two accumulators per row: scalars for one row per lane, packed pairs
+      // of rows (fma.rn.f32x2) for two or four
+      constexpr int NP = RPL >= 2 ? RPL / 2 : 1;
       float a0[RPL], a1[RPL];
+      uint64_t p0[NP], p1[NP];
 #pragma unroll
       for (int i = 0; i < RPL; ++i) a0[i] = a1[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) p0[i] = p1[i] = 0ull;
       auto finish_bin = [&]() {
         const uint4 c = C[l];
         const float A = __uint_as_float(c.y);
         float ys[RPL];
+        if constexpr (RPL >= 2) {
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          ys[i] = a0[i] + a1[i];
-          a0[i] = a1[i] = 0.f;
+          for (int i = 0; i < NP; ++i) {
+            float x0, x1, y0, y1;
+            unpack2(p0[i], x0, x1);
+            unpack2(p1[i], y0, y1);
+            ys[2 * i] = x0 + y0;
+            ys[2 * i + 1] = x1 + y1;
+            p0[i] = p1[i] = 0ull;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RPL; ++i) {
+            ys[i] = a0[i] + a1[i];
+            a0[i] = a1[i] = 0.f;
+          }
         }
         if (HW) {  // both halves end with the same sum (FP32 addition commutes)
 #pragma unroll
@@ -748,32 +810,62 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
         }
         ++l;
       };
-      auto step = [&](uint32_t q) {
+      auto step = [&](const QuadWords<EntT> &qw) {
         uint32_t e[4], w0;
-        lds_quad_raw<EntT>(eb + q * uint32_t(4 * sizeof(EntT)), e, w0);
+        decode_quad<EntT>(qw, e, w0);
         const float sgn = (w0 & EntFlags<EntT>::kNeg) ? -1.f : 1.f;
-        float v0[RPL], v1[RPL], v2[RPL], v3[RPL];
-        lds_x<RPL>(xb + e[0], v0);
-        lds_x<RPL>(xb + e[1], v1);
-        lds_x<RPL>(xb + e[2], v2);
-        lds_x<RPL>(xb + e[3], v3);
+        // x * (+-1) is exact: each fma is one rounded addition
+        if constexpr (RPL >= 2) {
+          const uint64_t s2 = pack2(sgn, sgn);
+          uint64_t v0[NP], v1[NP], v2[NP], v3[NP];
+          lds_x2<NP>(xb + e[0], v0);
+          lds_x2<NP>(xb + e[1], v1);
+          lds_x2<NP>(xb + e[2], v2);
+          lds_x2<NP>(xb + e[3], v3);
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {  // x * (+-1) is exact: each fma is one rounded addition
-          a0[i] = __fmaf_rn(v0[i], sgn, a0[i]);
-          a1[i] = __fmaf_rn(v1[i], sgn, a1[i]);
-          a0[i] = __fmaf_rn(v2[i], sgn, a0[i]);
-          a1[i] = __fmaf_rn(v3[i], sgn, a1[i]);
+          for (int i = 0; i < NP; ++i) {
+            p0[i] = ffma2(v0[i], s2, p0[i]);
+            p1[i] = ffma2(v1[i], s2, p1[i]);
+            p0[i] = ffma2(v2[i], s2, p0[i]);
+            p1[i] = ffma2(v3[i], s2, p1[i]);
+          }
+        } else {
+          float v0[RPL], v1[RPL], v2[RPL], v3[RPL];
+          lds_x<RPL>(xb + e[0], v0);
+          lds_x<RPL>(xb + e[1], v1);
+          lds_x<RPL>(xb + e[2], v2);
+          lds_x<RPL>(xb + e[3], v3);
+#pragma unroll
+          for (int i = 0; i < RPL; ++i) {
+            a0[i] = __fmaf_rn(v0[i], sgn, a0[i]);
+            a1[i] = __fmaf_rn(v1[i], sgn, a1[i]);
+            a0[i] = __fmaf_rn(v2[i], sgn, a0[i]);
+            a1[i] = __fmaf_rn(v3[i], sgn, a1[i]);
+          }
         }
         if (w0 & EntFlags<EntT>::kEnd) finish_bin();
       };
-      if (HW) {  // quad pairs: bins (and so the warp ranges) start at even quads
-        const uint32_t pend = rn.y >> 1;
-#pragma unroll 1
-        for (uint32_t pq = rb.y >> 1; pq < pend; ++pq) step(2 * pq + uint32_t(h));
-      } else {
+      // The flat loop over the range's quads (split bins: half h takes quads
+      // 2k + h; bins, and so the ranges, start at even quads and both halves
+      // take the same number of steps).  The next quad's entries are loaded
+      // one step ahead, so that their shared-memory latency overlaps this
+      // step's operand loads; the last step re-reads its own range's last quad.
+      {
+        constexpr uint32_t kQB = uint32_t(4 * sizeof(EntT));
+        constexpr uint32_t qs = HW ? 2u : 1u;
         const uint32_t qend = rn.y;
+        uint32_t q = rb.y + uint32_t(h);
+        if (q < qend) {
+          QuadWords<EntT> cur;
+          lds_quad_words<EntT>(eb + q * kQB, cur);
 #pragma unroll 1
-        for (uint32_t q = rb.y; q < qend; ++q) step(q);
+          for (; q < qend; q += qs) {
+            QuadWords<EntT> nxt;
+            lds_quad_words<EntT>(eb + min(q + qs, qend - 1) * kQB, nxt);
+            step(cur);
+            cur = nxt;
+          }
+        }
       }
       // partial keys of this warp -> the (row, table) slots
 #pragma unroll

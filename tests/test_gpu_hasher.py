@@ -27,7 +27,7 @@ def test_hasher_uneven_batches_equal_lsh_hash(kind, d, m, L, dims, mdims, dtype)
     fam = lsh.Family(kind, d, m, L, w=4.0, seed=77, dims=dims, mdims=mdims)
     h = lsh.Hasher(fam, dtype=dtype, max_rows=140000)
     # sizes: one bucket twice (9,000 and 12,000 -> 16,384), the smallest
-    # bucket (1, 100, 8,191), a large batch that the autotuner times first
+    # bucket (1, 100, 8,191), and two larger buckets (131,077 and 70,000 rows)
     sizes = [9000, 12000, 1, 100, 8191, 131077, 70000, 16384]
     big = _rows(max(sizes) + len(sizes), d, seed=d + L, dtype=dtype)
     for i, n in enumerate(sizes):
