@@ -93,22 +93,55 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
 }
 
 // Exclusive scan, in place, of cnt[t][0..len) for each table t (grid.x = table).
-// Optionally writes the table total to total_out[t].
+// Optionally writes the table total to total_out[t].  Each warp owns a
+// contiguous segment, read 32 consecutive words at a time (coalesced) with
+// eight such loads in flight: a first pass sums the segment, a block scan of
+// the warp sums gives each warp its base, and a second pass scans and writes.
+constexpr int kScanBatch = 8;
 __global__ void __launch_bounds__(1024) scan_rows(uint32_t *__restrict__ cnt, int64_t len,
                                                   int64_t *__restrict__ total_out) {
   __shared__ uint32_t warp_sums[33];
   uint32_t *c = cnt + int64_t(blockIdx.x) * len;
-  const int64_t per = (len + blockDim.x - 1) / blockDim.x;
-  const int64_t beg = int64_t(threadIdx.x) * per;
-  const int64_t end = beg + per < len ? beg + per : len;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t seg = ((len + nw - 1) / nw + 31) & ~int64_t(31);
+  const int64_t beg = int64_t(warp) * seg;
+  const int64_t end = beg + seg < len ? beg + seg : len;
   uint32_t s = 0;
-  for (int64_t i = beg; i < end; ++i) s += c[i];
+  for (int64_t i0 = beg; i0 < end; i0 += 32 * kScanBatch) {
+    uint32_t v[kScanBatch];
+#pragma unroll
+    for (int b = 0; b < kScanBatch; ++b) {
+      const int64_t i = i0 + b * 32 + lane;
+      v[b] = i < end ? c[i] : 0u;
+    }
+#pragma unroll
+    for (int b = 0; b < kScanBatch; ++b) s += v[b];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  // the warp totals, scanned by the block (one value per warp, in lane 0)
   uint32_t total;
-  uint32_t run = block_exclusive_scan(s, warp_sums, total);
-  for (int64_t i = beg; i < end; ++i) {
-    const uint32_t v = c[i];
-    c[i] = run;
-    run += v;
+  const uint32_t wbase = block_exclusive_scan(lane == 0 ? s : 0u, warp_sums, total);
+  uint32_t run = __shfl_sync(0xffffffffu, wbase, 0);
+  for (int64_t i0 = beg; i0 < end; i0 += 32 * kScanBatch) {
+    uint32_t v[kScanBatch];
+#pragma unroll
+    for (int b = 0; b < kScanBatch; ++b) {
+      const int64_t i = i0 + b * 32 + lane;
+      v[b] = i < end ? c[i] : 0u;
+    }
+#pragma unroll
+    for (int b = 0; b < kScanBatch; ++b) {
+      uint32_t x = v[b];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      const int64_t i = i0 + b * 32 + lane;
+      if (i < end) c[i] = run + x - v[b];
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
   }
   if (total_out && threadIdx.x == 0) total_out[blockIdx.x] = int64_t(total);
 }
