@@ -873,6 +873,24 @@ def main():
                               "flagged_per_entry": st["n_flagged"] / max(1, st["n_entries"]),
                               "changed": st["n_changed"]}
             f2.close()
+        # the same hash with the int32 codes [n, L, m] written too (12.8 GB at the
+        # headline): the HBM view of hashcode generation
+        codes = torch.empty((n, L, m), dtype=torch.int32, device=dev)
+        fam.hash_into(mtx, lsh._ptr(codes), lsh._ptr(keys), None)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            fam.hash_into(mtx, lsh._ptr(codes), lsh._ptr(keys), None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / 3
+        cbytes = bytes_alg + float(codes.numel()) * 4
+        variants["cs_e2lsh_codes_out"] = {"hash_ms": cms, "points_per_s": n / (cms / 1e3),
+                                          "algorithmic_bytes": cbytes,
+                                          "hbm_frac": cbytes / (cms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                          "note": "keys and int32 codes [n, L, m] written"}
+        del codes
+        torch.cuda.empty_cache()
         # CSSRP-L (Table 1): l bins per coordinate, l times the count sketch's adds
         for lc in (2, 4):
             fa = dict(_workload(args.workload, "cs_srp")[1], kind="csl_srp", l=lc)
