@@ -675,7 +675,7 @@ cudaError_t launch_sketch_csr(const SketchLaunch &p, const int64_t *rowptr, cons
   a.smem = a.off_tab + (stage ? int(tab_bytes) : 0);
   if (a.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   int per_sm = (228 * 1024) / (a.smem + 1024);
-  per_sm = std::max(1, std::min(per_sm, 2048 / (W * kWarp)));
+  per_sm = std::max(1, std::min(per_sm, 2));  // __launch_bounds__(256, 2): two CTAs' registers per SM
   const int64_t want = int64_t(sm_count()) * per_sm;
   const int64_t need = (p.n + W - 1) / W;
   const int grid = int(want < need ? want : need);

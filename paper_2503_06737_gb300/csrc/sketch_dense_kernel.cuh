@@ -718,6 +718,39 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
       // epilogue
       const uint2 rb = rng[tl * (kMaxWpt + 1) + sub], rn = rng[tl * (kMaxWpt + 1) + sub + 1];
       int l = int(rb.x);
+      // full outputs: the codes and projections of a row's last four bins,
+      // written four at a time (one 16-byte store per row and output) when
+      // the bin index reaches a multiple of four, and at the range's ends
+      int cq[EPR][4];
+      float pq[EPR][4];
+      const bool vec_out = (m & 3) == 0 && (reinterpret_cast<uintptr_t>(p.codes) & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(p.proj) & 15) == 0;
+      auto put_out = [&](int k, int64_t row, int code, float y) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          cq[k][j] = cq[k][j + 1];
+          pq[k][j] = pq[k][j + 1];
+        }
+        cq[k][3] = code;
+        pq[k][3] = y;
+        if ((l & 3) != 3 && l != int(rn.x) - 1) return;
+        if (row >= n) return;
+        const int64_t o = (row * p.L + t) * m;
+        if (vec_out && (l & 3) == 3 && l - 3 >= int(rb.x)) {
+          if (p.codes) *reinterpret_cast<int4 *>(p.codes + o + l - 3) = make_int4(cq[k][0], cq[k][1], cq[k][2], cq[k][3]);
+          if (p.proj) *reinterpret_cast<float4 *>(p.proj + o + l - 3) = make_float4(pq[k][0], pq[k][1], pq[k][2], pq[k][3]);
+          return;
+        }
+        const int lo = max(l & ~3, int(rb.x));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int bl = l - 3 + j;
+          if (bl >= lo) {
+            if (p.codes) p.codes[o + bl] = cq[k][j];
+            if (p.proj) p.proj[o + bl] = pq[k][j];
+          }
+        }
+      };
       // two accumulators per row: scalars for one row per lane, packed pairs
       // of rows (fma.rn.f32x2) for two or four
       constexpr int NP = RPL >= 2 ? RPL / 2 : 1;
@@ -782,7 +815,7 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
             novf += (o.ev >> 2) & 1;
           }
           if (SRP) {
-            if (FULL && p.proj && row < n) p.proj[(row * p.L + t) * m + l] = y;
+            if (FULL && p.proj) put_out(k, row, 0, y);
             if (m <= 64) {
               if (l < 32)
                 ha[k] |= uint32_t(code) << l;
@@ -799,10 +832,7 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
           } else {
             if (FULL) {
               if (bad[ri]) code = INT32_MIN;
-              if (row < n) {
-                if (p.codes) p.codes[(row * p.L + t) * m + l] = code;
-                if (p.proj) p.proj[(row * p.L + t) * m + l] = y;
-              }
+              if (p.codes || p.proj) put_out(k, row, code, y);
             }
             ha[k] += uint32_t(code) * c.z;
             hb[k] += uint32_t(code) * c.w;
