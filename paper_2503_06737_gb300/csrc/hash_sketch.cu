@@ -208,10 +208,11 @@ cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stre
 // Autotuner: the first batch of at least kTuneRows rows of a shape (device,
 // kind, d, m, L, modes, dtype) times every candidate plan (three launches
 // after a warm-up) on its first kTuneRows rows -- keys only, no recheck
-// queue, into the caller's key buffer,
-// which the real launch then overwrites -- and keeps the fastest.  It is
-// skipped while the stream is being captured (the default plan is used).
-// Every plan computes the same codes, and a plan fits any row count.
+// queue, into the caller's key buffer, which the real launch then
+// overwrites -- and keeps the fastest; later batches of the shape with at
+// least two of its tiles per SM use it too.  The timing is skipped while the
+// stream is being captured (the default plan is used).  Every plan computes
+// the same codes, and a plan fits any row count.
 constexpr int64_t kTuneRows = 524288;  // enough tiles per CTA that the tail of the last wave is small
 
 struct TuneKey {
@@ -224,7 +225,7 @@ std::map<TuneKey, Plan> g_tuned;
 
 Plan tuned_plan(const SketchLaunch &p, cudaStream_t stream, bool may_time = true) {
   const Plan dflt = make_plan(p.d, p.m, p.L, p.cap, p.n);
-  if (p.n < kTuneRows || dflt.smem <= 0) return dflt;
+  if (dflt.smem <= 0) return dflt;
   TuneKey key;
   std::memset(&key, 0, sizeof(key));
   cudaGetDevice(&key.dev);
@@ -240,10 +241,16 @@ Plan tuned_plan(const SketchLaunch &p, cudaStream_t stream, bool may_time = true
     key.mdims[k] = p.mdims[k];
   }
   {
+    // a shape tuned before serves any batch that gives every SM two tiles of
+    // the tuned plan (smaller ones keep the default, sized for them)
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
-    if (it != g_tuned.end()) return it->second;
+    if (it != g_tuned.end()) {
+      const int64_t tiles = (p.n + tile_rows(it->second) - 1) / tile_rows(it->second);
+      return tiles >= 2 * int64_t(num_sms()) ? it->second : dflt;
+    }
   }
+  if (p.n < kTuneRows) return dflt;
   if (!may_time) return dflt;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return dflt;
