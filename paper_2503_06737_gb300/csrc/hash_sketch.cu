@@ -65,7 +65,7 @@ Plan plan_of(int d, int m, int L, int cap, int RPL, int RG, int WPT, int Lg, int
   if (W < 4) W = 4;
   pl.W = W;
   pl.dp = odd_stride(d);
-  pl.cap = hw ? cap + 4 * m : cap;
+  pl.cap = (hw ? cap + 4 * m : cap) + 8;  // + two spare quads the loop's look-ahead may read
   const int R = tile_rows(pl);
   int off = 0;
   pl.off_ent = off;

@@ -879,19 +879,20 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
       // 2k + h; bins, and so the ranges, start at even quads and both halves
       // take the same number of steps).  The next quad's entries are loaded
       // one step ahead, so that their shared-memory latency overlaps this
-      // step's operand loads; the last step re-reads its own range's last quad.
+      // step's operand loads.
       {
-        constexpr uint32_t kQB = uint32_t(4 * sizeof(EntT));
-        constexpr uint32_t qs = HW ? 2u : 1u;
-        const uint32_t qend = rn.y;
-        uint32_t q = rb.y + uint32_t(h);
-        if (q < qend) {
+        constexpr uint32_t kStep = uint32_t(4 * sizeof(EntT)) * (HW ? 2u : 1u);  // bytes per step
+        uint32_t qa = eb + (rb.y + uint32_t(h)) * uint32_t(4 * sizeof(EntT));
+        const uint32_t qa_end = eb + rn.y * uint32_t(4 * sizeof(EntT));
+        if (qa < qa_end) {
           QuadWords<EntT> cur;
-          lds_quad_words<EntT>(eb + q * kQB, cur);
+          lds_quad_words<EntT>(qa, cur);
 #pragma unroll 1
-          for (; q < qend; q += qs) {
+          for (; qa < qa_end; qa += kStep) {
+            // one step ahead; past the range's end this reads the next
+            // range's quads or the table's two spare quads, never used
             QuadWords<EntT> nxt;
-            lds_quad_words<EntT>(eb + min(q + qs, qend - 1) * kQB, nxt);
+            lds_quad_words<EntT>(qa + kStep, nxt);
             step(cur);
             cur = nxt;
           }
