@@ -240,8 +240,9 @@ void lsh_family_destroy(lsh_family_t fam);
  * Stream-ordered and asynchronous, with two exceptions: the first dense-row
  * CS/HCS call of a shape (device, kind, d, m, L, modes, dtype) with at least
  * 524,288 rows times the candidate tile plans of the hashing kernel on its
- * first 524,288 rows and waits for them (once per shape; skipped while the
- * stream is captured); and calls with stats synchronise.  Temporaries come
+ * first 524,288 rows and on half as many, and waits for them (once per
+ * shape; skipped while the stream is captured); and calls with stats
+ * synchronise.  Temporaries come
  * from the device's stream-ordered memory pool: the recheck queue of a
  * dense-row CS/HCS batch of 8,192 rows or more (16 B per 256 entries of
  * n*L*m, plus 1 MiB), and for a tensor-core call 32 B of row records per row

@@ -207,13 +207,14 @@ cudaError_t launch_plan(const SketchLaunch &p, const Plan &pl, cudaStream_t stre
 
 // Autotuner: the first batch of at least kTuneRows rows of a shape (device,
 // kind, d, m, L, modes, dtype) times every candidate plan (three launches
-// after a warm-up) on its first kTuneRows rows -- keys only, no recheck
-// queue, into the caller's key buffer, which the real launch then
-// overwrites -- and keeps the fastest; later batches of the shape with at
-// least two of its tiles per SM use it too.  The timing is skipped while the
-// stream is being captured (the default plan is used).  Every plan computes
-// the same codes, and a plan fits any row count.
-constexpr int64_t kTuneRows = 524288;  // enough tiles per CTA that the tail of the last wave is small
+// after a warm-up) on its first kTuneRows rows and on half as many -- keys
+// only, no recheck queue, into the caller's key buffer, which the real
+// launch then overwrites -- and keeps the plan whose fixed cost plus cost
+// per row predicts the least time for the batch; later batches of the shape
+// with at least two of its tiles per SM use it too.  The timing is skipped
+// while the stream is being captured (the default plan is used).  Every plan
+// computes the same codes, and a plan fits any row count.
+constexpr int64_t kTuneRows = 524288;
 
 struct TuneKey {
   int dev, kind, d, m, L, N, dtype, cap;
@@ -269,18 +270,29 @@ Plan tuned_plan(const SketchLaunch &p, cudaStream_t stream, bool may_time = true
     if (e0) cudaEventDestroy(e0);
     return dflt;
   }
-  Plan best = dflt;
-  float best_ms = 1e30f;
-  for (const Plan &pl : cands) {
-    if (launch_plan(q, pl, stream) != cudaSuccess) continue;  // warm-up (and attribute setting)
+  // each candidate on kTuneRows and on half as many rows: the difference is
+  // its cost per row, the rest a fixed cost (table staging, the last wave);
+  // the plan with the least predicted time for the caller's row count wins
+  auto timed = [&](const Plan &pl, int64_t rows, float &ms) {
+    q.n = rows;
     cudaEventRecord(e0, stream);
     bool ok = true;
     for (int r = 0; r < 3 && ok; ++r) ok = launch_plan(q, pl, stream) == cudaSuccess;  // three: less noise
     cudaEventRecord(e1, stream);
-    float ms = 0.f;
-    if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
-    if (ms < best_ms) {
-      best_ms = ms;
+    return ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  };
+  Plan best = dflt;
+  double best_pred = 1e300;
+  for (const Plan &pl : cands) {
+    q.n = kTuneRows;
+    if (launch_plan(q, pl, stream) != cudaSuccess) continue;  // warm-up (and attribute setting)
+    float full = 0.f, half = 0.f;
+    if (!timed(pl, kTuneRows, full) || !timed(pl, kTuneRows / 2, half)) continue;
+    const double per_row = std::max(0.0, double(full - half) / double(kTuneRows / 2));
+    const double fixed = std::max(0.0, double(full) - per_row * double(kTuneRows));
+    const double pred = fixed + per_row * double(p.n);
+    if (pred < best_pred) {
+      best_pred = pred;
       best = pl;
     }
   }
