@@ -245,9 +245,10 @@ void lsh_family_destroy(lsh_family_t fam);
  * synchronise.  Temporaries come
  * from the device's stream-ordered memory pool: the recheck queue of a
  * dense-row CS/HCS batch of 8,192 rows or more (16 B per 256 entries of
- * n*L*m, plus 1 MiB), and for a tensor-core call 32 B of row records per row
- * plus a queue of 16 B per 256 projections (plus 1 MiB) -- 512 MiB for
- * 4,000,000 rows with m*L = 2048.
+ * n*L*m, plus 1 MiB), and for a tensor-core call 36 B of row records and
+ * counts per row plus two queues of 16 B per 256 projections (plus 1 MiB
+ * each; the second holds the first grouped by row) -- 1.2 GiB for 4,000,000
+ * rows with m*L = 2048.
  */
 lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t *keys,
                     float *proj, lsh_hash_stats *stats, void *stream);

@@ -178,7 +178,7 @@ lsh_status hash_impl(lsh_family_s *f, const lsh_matrix *X, void *codes, uint64_t
     const cudaError_t e = launch_tc_dense(p, gtc, f->d_Gt, f->d_gnc, f->d_Gint, scratch, stream);
     cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core dense hash");
-    count_launches(3);
+    count_launches(6);  // row records, the tensor-core kernel, the queue grouping (3), the recheck
     return LSH_OK;
   }
   if (kind_is_dense(d.kind)) {

@@ -828,6 +828,96 @@ __global__ void __launch_bounds__(kThreads, 1) tc_dense_kernel(const __grid_cons
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// Grouping of the recheck queue by row (a counting sort): the entries of one
+// row end up adjacent, so the recheck warps that take them read the row from
+// HBM once and from L1 after that.  Order inside a row is immaterial.
+__global__ void __launch_bounds__(256) queue_row_count(const int4 *__restrict__ queue,
+                                                       const uint32_t *__restrict__ qcount, uint32_t qcap,
+                                                       uint32_t *__restrict__ cnt) {
+  const int64_t c = min(int64_t(*qcount), int64_t(qcap));
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < c; i += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&cnt[uint32_t(queue[i].x)], 1u);
+}
+
+// Exclusive scan of cnt[0..n) in place over kScanBlocks blocks of 1024
+// threads, in two launches.  Block b owns a contiguous segment; inside it each
+// warp owns a contiguous run read 32 words at a time (eight loads in flight).
+// scan_row_counts<false> writes each block's total to sums[b];
+// scan_row_counts<true> scans the totals of the blocks before it and rewrites
+// its segment with exclusive prefixes.
+constexpr int kScanBlocks = 128;
+template <bool WRITE>
+__global__ void __launch_bounds__(1024) scan_row_counts(uint32_t *__restrict__ cnt, int64_t n,
+                                                        uint32_t *__restrict__ sums) {
+  __shared__ uint32_t ws[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t bseg = (n + kScanBlocks - 1) / kScanBlocks;
+  const int64_t b0 = int64_t(blockIdx.x) * bseg, b1 = min(b0 + bseg, n);
+  const int64_t seg = ((bseg + 31) / 32 + 31) & ~int64_t(31);
+  const int64_t beg = b0 + int64_t(warp) * seg, end = min(beg + seg, b1);
+  constexpr int B = 8;
+  uint32_t s = 0;
+  for (int64_t i0 = beg; i0 < end; i0 += 32 * B) {
+    uint32_t v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = i0 + k * 32 + lane < end ? cnt[i0 + k * 32 + lane] : 0u;
+#pragma unroll
+    for (int k = 0; k < B; ++k) s += v[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t x = ws[lane];
+    uint32_t y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += u;
+    }
+    ws[lane] = y - x;  // exclusive prefix of the warps
+    if (!WRITE && lane == 31) sums[blockIdx.x] = y;
+  }
+  if (!WRITE) return;
+  // the totals of the blocks before this one (at most kScanBlocks words)
+  if (warp == 1) {
+    uint32_t t = 0;
+    for (int i = lane; i < int(blockIdx.x); i += 32) t += sums[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) ws[32] = t;
+  }
+  __syncthreads();
+  uint32_t run = ws[32] + ws[warp];
+  for (int64_t i0 = beg; i0 < end; i0 += 32 * B) {
+    uint32_t v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = i0 + k * 32 + lane < end ? cnt[i0 + k * 32 + lane] : 0u;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      uint32_t x = v[k];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+      }
+      if (i0 + k * 32 + lane < end) cnt[i0 + k * 32 + lane] = run + x - v[k];
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) queue_row_scatter(const int4 *__restrict__ queue,
+                                                         const uint32_t *__restrict__ qcount, uint32_t qcap,
+                                                         uint32_t *__restrict__ off, int4 *__restrict__ out) {
+  const int64_t c = min(int64_t(*qcount), int64_t(qcap));
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < c; i += int64_t(gridDim.x) * blockDim.x) {
+    const int4 r = queue[i];
+    out[atomicAdd(&off[uint32_t(r.x)], 1u)] = r;
+  }
+}
+
 // The queued entries, 32 to a warp: the whole warp computes the exact sum of
 // each entry in turn (lane k keeps entry k's), then every lane converts and
 // discretises its own entry -- the FP64 steps run once for 32 entries -- and
@@ -1018,17 +1108,19 @@ int tc_chunk_ktiles(int d, bool fp8) {
   return (ktiles + NCH - 1) / NCH;
 }
 
-// Scratch of one call: the row records [n][8] floats, the queue counter and
-// the recheck queue (16 bytes an entry, one slot per 256 projections: the
-// flag rate of Gaussian rows at w = 4 grows about as d^2 and is 2.3e-3 at
-// d = 960; entries beyond it are rechecked inside the main kernel, slowly).
+// Scratch of one call: the row records [n][8] floats, the queue counter, the
+// recheck queue (16 bytes an entry, one slot per 256 projections: the flag
+// rate of Gaussian rows at w = 4 grows about as d^2 and is 2.3e-3 at d = 960;
+// entries beyond it are rechecked inside the main kernel, slowly), and for
+// the grouping by row a count per row and a second queue.
 static int64_t tc_queue_cap(int64_t n, int64_t ML) {
   return std::min<int64_t>(n * ML / 256 + 65536, int64_t(1) << 28);
 }
 static int64_t tc_align16(int64_t b) { return (b + 15) & ~int64_t(15); }
 
 size_t tc_dense_scratch_bytes(int64_t n, int64_t ML) {
-  return size_t(tc_align16(n * XNC_LD * 4) + 16 + tc_queue_cap(n, ML) * 16);
+  return size_t(tc_align16(n * XNC_LD * 4) + 16 + 2 * tc_queue_cap(n, ML) * 16 + tc_align16(n * 4) +
+                4 * kScanBlocks);
 }
 
 bool tc_dense_supported(const lsh_family_desc &fd, const lsh_matrix *X) {
@@ -1059,6 +1151,10 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float 
   float *xnc_scratch = static_cast<float *>(scratch);
   uint32_t *qcount = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + tc_align16(p.n * XNC_LD * 4));
   int4 *queue = reinterpret_cast<int4 *>(qcount + 4);
+  const int64_t qcap = tc_queue_cap(p.n, int64_t(p.m) * p.L);
+  int4 *queue_by_row = queue + qcap;
+  uint32_t *row_cnt = reinterpret_cast<uint32_t *>(queue_by_row + qcap);
+  uint32_t *scan_sums = row_cnt + tc_align16(p.n * 4) / 4;  // [kScanBlocks]
   cudaError_t e = cudaMemsetAsync(qcount, 0, 16, stream);
   if (e != cudaSuccess) return e;
   row_chunk_norms<<<(unsigned)((p.n + 7) / 8), 256, 0, stream>>>(p.X, fp8 ? 1 : 0, p.row_scale, p.n, p.d, p.ld,
@@ -1136,6 +1232,16 @@ cudaError_t launch_tc_dense(const SketchLaunch &p, const void *Gtc, const float 
   kern<<<grid, kThreads, smem, stream>>>(mA, mB, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // the queue grouped by row, then the recheck over the grouped copy
+  e = cudaMemsetAsync(row_cnt, 0, size_t(p.n) * 4, stream);
+  if (e != cudaSuccess) return e;
+  queue_row_count<<<unsigned(sms) * 8, 256, 0, stream>>>(queue, qcount, a.qcap, row_cnt);
+  scan_row_counts<false><<<kScanBlocks, 1024, 0, stream>>>(row_cnt, p.n, scan_sums);
+  scan_row_counts<true><<<kScanBlocks, 1024, 0, stream>>>(row_cnt, p.n, scan_sums);
+  queue_row_scatter<<<unsigned(sms) * 8, 256, 0, stream>>>(queue, qcount, a.qcap, row_cnt, queue_by_row);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  a.queue = queue_by_row;
   tc_recheck_kernel<<<unsigned(sms) * 8, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
