@@ -43,6 +43,8 @@ CASES = [
     ("cs_e2lsh", 33, 37, 1, 1, None, None, torch.float32),              # m = 1, L = 1
     ("cs_srp", 1, 64, 64, 2, None, None, torch.float32),                # n = 1, m = 64
     ("hcs_srp", 129, 64, 8, 3, [4, 4, 4], [2, 2, 2], torch.float32),
+    ("cs_e2lsh", 300, 200, 13, 7, None, None, torch.float32),           # m not a multiple of 4: scalar code stores
+    ("hcs_srp", 150, 200, 26, 5, [10, 20], [2, 13], torch.float16),
 ]
 
 
