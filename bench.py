@@ -655,12 +655,30 @@ def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=5e6, seconds_p
     out["exact_knn_bruteforce"] = {"batch": 4096, "batch_ms": bms, "qps": 4096 / (bms / 1e3), "recall10": 1.0,
                                    "note": "torch FP32 matrix products + top-k over all 10,000,000 rows"}
     log(f"serving: brute-force exact k-NN {4096 / (bms / 1e3):.0f} queries/s")
+    # the same scan with TF32 tensor-core products (the FP64 refinement of each
+    # chunk's best 2k keeps the order exact unless TF32 moves a neighbour out)
+    tf32_prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        e0.record(stream)
+        ids_tf, _ = measure.exact_knn(X, Qb, 10)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32_prev
+    tms = e0.elapsed_time(e1)
+    ids_fp, _ = measure.exact_knn(X, Qb[:256], 10)
+    out["exact_knn_bruteforce_tf32"] = {
+        "batch": 4096, "batch_ms": tms, "qps": 4096 / (tms / 1e3),
+        "recall10_vs_fp32": measure.recall_at_k(ids_tf[:256].cpu().numpy(), ids_fp.cpu().numpy()),
+        "note": "TF32 tensor-core products + torch top-k (which takes most of the time) + FP64 refinement"}
+    log(f"serving: brute-force k-NN with TF32 products {4096 / (tms / 1e3):.0f} queries/s")
     for kind, m, dims, mdims in (("hcs_e2lsh", wl["m_hcs"], wl["hcs_dims"], wl["hcs_mdims"]),
                                  ("cs_e2lsh", wl["m_cs"], None, None)):
         chosen = None
         tried = []
         best = None
-        for w in (4.0, 8.0, 16.0, 24.0, 32.0, 48.0, 64.0, 96.0):
+        for w in (4.0, 8.0, 16.0, 24.0, 32.0, 36.0, 40.0, 44.0, 48.0, 56.0, 64.0, 96.0):
             fam = lsh.Family(kind, wl["d"], m, wl["L"], w=w, seed=42, dims=dims, mdims=mdims)
             idx = fam.build_index(X, keep_data=True)
             res = idx.query(Qt, k=10, stats=True)
