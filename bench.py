@@ -678,7 +678,7 @@ def serving_bench(dev, e0, e1, stream, max_requests=200, max_cand=5e6, seconds_p
         chosen = None
         tried = []
         best = None
-        for w in (4.0, 8.0, 16.0, 24.0, 32.0, 36.0, 40.0, 44.0, 48.0, 56.0, 64.0, 96.0):
+        for w in (4.0, 8.0, 16.0, 24.0, 32.0, 36.0, 40.0, 42.0, 44.0, 46.0, 48.0, 56.0, 64.0, 96.0):
             fam = lsh.Family(kind, wl["d"], m, wl["L"], w=w, seed=42, dims=dims, mdims=mdims)
             idx = fam.build_index(X, keep_data=True)
             res = idx.query(Qt, k=10, stats=True)
