@@ -325,8 +325,32 @@ lsh_status lsh_hasher_info(lsh_hasher_t h, int64_t *captures, int64_t *replays);
 void lsh_hasher_destroy(lsh_hasher_t h);
 
 /*
+ * The sort behind every table build (lsh_build_index, lsh_index_rebuild,
+ * lsh_index_rebuild_host, lsh_build_tables_static), process-wide:
+ *   0  automatic (the default): the bucket sort for 2,048 <= n <= 1,126,400
+ *      rows, else the global passes;
+ *   1  global passes: a stable LSD radix sort, 8 passes of 8 bits over all
+ *      of every table's (key, id) pairs;
+ *   2  the bucket sort at any n: per table, the bits on which its keys
+ *      differ are found, one stable global pass on the 8 highest of them
+ *      cuts the table into 256 buckets, and one CTA per bucket finishes it:
+ *      a bucket of up to 5,120 keys in shared memory (one counting pass on
+ *      the next 8 bits, then each key placed by comparisons inside its group
+ *      of equal such bits), larger buckets and buckets with groups of more
+ *      than 96 keys by counting passes on every lower digit through global
+ *      memory, skipping digits on which the table's or the bucket's keys
+ *      agree.
+ * All modes give the same tables bit for bit; the mode only moves time
+ * (buckets well above 5,120 keys, from more than about 1.1 M rows or from
+ * clustered keys, are slower in mode 2).  Returns LSH_EINVAL for any other
+ * mode.  Set it between builds: a build reads it when it is enqueued.
+ */
+lsh_status lsh_set_sort_mode(int32_t mode);
+
+/*
  * Build the L hash tables of Sec. 3.1 over X: hash (keys only), then per
- * table a stable device radix sort of (key, id) and the bucket segmentation.
+ * table a stable device sort of (key, id) (lsh_set_sort_mode) and the bucket
+ * segmentation.
  *   keep_data  nonzero: the index keeps a device copy of X (dense rows) for
  *              lsh_query's exact rerank; zero: it keeps only the tables.
  *   out        host pointer receiving the handle (owns its device memory).
@@ -346,7 +370,7 @@ lsh_status lsh_index_rebuild(lsh_index_t idx, const lsh_matrix *X, void *stream)
 /*
  * The same rebuild from rows in HOST memory (X->values a host pointer, dense
  * f32/bf16/f16 rows; pinned memory for full copy speed): the rows go to the
- * device in chunks of chunk_rows (0: max(131072, n/16)) on a stream of the
+ * device in chunks of chunk_rows (0: max(32768, n/32)) on a stream of the
  * call's own while the previous chunk is hashed on `stream` -- the transfer
  * and the hashing overlap -- then the tables are sorted on `stream`.  When the
  * index keeps data the rows land in its copy, else in two staging buffers
@@ -485,8 +509,9 @@ void lsh_server_destroy(lsh_server_t srv);
  *             device outputs laid out as in lsh_index_export ([L][n], [L][n],
  *             [L][n+1], [L]); the caller owns them.
  *   Limits: n * L <= LSH_STATIC_MAX_PAIRS (2^20), and the sort scratch --
- *   keys twice (8 n L bytes each), ids (4 n L) and the digit histograms
- *   (1024 ceil(n / 4096) L), each rounded up to 256 bytes -- at most 24 MiB;
+ *   keys twice (8 n L bytes each), ids (4 n L), the digit histograms
+ *   (1024 ceil(n / 4096) L) and the bucket sort's key-spread words and
+ *   bucket list (1040 L + 4), each rounded up to 256 bytes -- at most 24 MiB;
  *   so with few rows and many tables (n = 64, L = 16384, say) a request
  *   within 2^20 pairs can still be refused.  Requests past either limit
  *   return LSH_EINVAL with a message naming the limit.  The first call on a device looks up the

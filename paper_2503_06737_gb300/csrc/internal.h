@@ -64,13 +64,6 @@ void sample_family(const lsh_family_desc &desc, HostFamily &hf);
 // multiple of four (the layout of the dense-row hashing kernel).
 int sketch_capacity(const HostFamily &hf);
 
-// The same table build with caller-provided scratch (no allocation); the
-// scratch must hold build_tables_scratch_bytes(n, L) bytes, 256-byte aligned.
-size_t build_tables_scratch_bytes(int64_t n, int32_t L);
-cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
-                                 uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out, void *scratch,
-                                 cudaStream_t stream);
-
 }  // namespace lsh
 
 struct lsh_family_s {
@@ -234,8 +227,11 @@ cudaError_t launch_query(const uint64_t *qkeys, int64_t q, int32_t L, int32_t k,
                          float *out_dist, unsigned long long *counters, void *scratch, int64_t scratch_q,
                          const int64_t *q_live, cudaStream_t stream);
 
-// Stable per-table radix sort of keys [L][n] with ids, then bucket segmentation.
-// Allocates its temporaries with cudaMallocAsync on `stream`.
+// Stable per-table sort of keys [L][n] with ids, then bucket segmentation:
+// the bucket sort (one global pass on the highest varying digit, buckets
+// finished on chip) when bucket_sort_used(n), else eight global 8-bit LSD
+// radix passes; both give the same arrays.  Allocates its temporaries with
+// cudaMallocAsync on `stream`.
 cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
                          uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out,
                          cudaStream_t stream);
@@ -243,6 +239,10 @@ cudaError_t build_tables(const uint64_t *keys, int64_t n, int32_t L, uint32_t *i
 // The same table build with caller-provided scratch (no allocation); the
 // scratch must hold build_tables_scratch_bytes(n, L) bytes, 256-byte aligned.
 size_t build_tables_scratch_bytes(int64_t n, int32_t L);
+// Sort mode of the table build: 0 automatic, 1 global LSD passes, 2 bucket
+// sort at any n.  Returns -1 for other values.
+int set_sort_mode(int mode);
+bool bucket_sort_used(int64_t n);
 cudaError_t build_tables_scratch(const uint64_t *keys, int64_t n, int32_t L, uint32_t *ids_out,
                                  uint64_t *ukeys_out, uint32_t *offsets_out, int64_t *nb_out, void *scratch,
                                  cudaStream_t stream);

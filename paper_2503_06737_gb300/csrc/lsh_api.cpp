@@ -600,6 +600,12 @@ lsh_status lsh_hash(lsh_family_t fam, const lsh_matrix *X, void *codes, uint64_t
   return st;
 }
 
+lsh_status lsh_set_sort_mode(int32_t mode) {
+  if (set_sort_mode(mode) != 0)
+    return fail(LSH_EINVAL, "sort mode must be 0 (automatic), 1 (global passes) or 2 (bucket sort)");
+  return LSH_OK;
+}
+
 lsh_status lsh_set_sketch_plan(int32_t rows_per_lane, int32_t row_groups, int32_t warps_per_table,
                                int32_t tables_per_cta, int32_t entry_bytes, int32_t split_bins) {
   const bool clear = rows_per_lane == 0 && row_groups == 0 && warps_per_table == 0 && tables_per_cta == 0 &&
@@ -714,7 +720,9 @@ lsh_status lsh_index_rebuild_host(lsh_index_t idx, const lsh_matrix *X, int64_t 
   if (chunk_rows < 0) return fail(LSH_EINVAL, "chunk_rows must be >= 0");
   const int64_t n = X->n;
   if (n == 0) return LSH_OK;
-  if (chunk_rows == 0) chunk_rows = std::max<int64_t>(131072, (n + 15) / 16);
+  // small chunks keep the hash of the last one, which no copy hides, short;
+  // below about 16,384 rows the per-chunk launches cost more than they save
+  if (chunk_rows == 0) chunk_rows = std::max<int64_t>(32768, (n + 31) / 32);
   chunk_rows = std::min(chunk_rows, n);
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const int L = idx->L;

@@ -97,6 +97,7 @@ SIGNATURES = [
     ("lsh_family_destroy", None, [P]),
     ("lsh_hash", ctypes.c_int, [P, ctypes.POINTER(Matrix), P, P, P, ctypes.POINTER(HashStats), P]),
     ("lsh_set_sketch_plan", ctypes.c_int, [ctypes.c_int32] * 6),
+    ("lsh_set_sort_mode", ctypes.c_int, [ctypes.c_int32]),
     ("lsh_get_sketch_plan", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, P]),
     ("lsh_build_index", ctypes.c_int, [P, ctypes.POINTER(Matrix), ctypes.c_int32, ctypes.POINTER(P), P]),
     ("lsh_index_rebuild", ctypes.c_int, [P, ctypes.POINTER(Matrix), P]),
@@ -148,6 +149,11 @@ def set_sketch_plan(rows_per_lane=0, row_groups=0, warps_per_table=0, tables_per
     """Pin the dense-row sketch kernel's plan process-wide (all zeros: autotuned)."""
     _check(lib().lsh_set_sketch_plan(rows_per_lane, row_groups, warps_per_table, tables_per_cta, entry_bytes,
                                      split_bins))
+
+
+def set_sort_mode(mode=0):
+    """Sort of the table builds, process-wide: 0 automatic, 1 global LSD passes, 2 bucket sort."""
+    _check(lib().lsh_set_sort_mode(int(mode)))
 
 
 def _check(st: int):

@@ -117,6 +117,15 @@ def test_sketch_plan_pin_validation(L):
     assert lib.lsh_set_sketch_plan(0, 0, 0, 0, 0, 0) == 0
 
 
+def test_sort_mode_validation(L):
+    """The sort-mode switch is host-only: 0, 1 and 2 are accepted, others refused."""
+    lib = L.lib()
+    for mode in (-1, 3, 7):
+        assert lib.lsh_set_sort_mode(mode) == 1, mode  # LSH_EINVAL
+    for mode in (1, 2, 0):
+        assert lib.lsh_set_sort_mode(mode) == 0, mode
+
+
 def test_merge_topk_against_restatement(L):
     """lsh_merge_topk (host only): the k best of the union by (distance,
     global id), from sorted per-shard lists with -1 / +inf tails; ties in
