@@ -765,13 +765,11 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
         const float A = __uint_as_float(c.y);
         float ys[RPL];
         if constexpr (RPL >= 2) {
+          // p0 * 1 + p1: one rounding per row, the same as the scalar sums
+          const uint64_t one2 = pack2(1.f, 1.f);
 #pragma unroll
           for (int i = 0; i < NP; ++i) {
-            float x0, x1, y0, y1;
-            unpack2(p0[i], x0, x1);
-            unpack2(p1[i], y0, y1);
-            ys[2 * i] = x0 + y0;
-            ys[2 * i + 1] = x1 + y1;
+            unpack2(ffma2(p0[i], one2, p1[i]), ys[2 * i], ys[2 * i + 1]);
             p0[i] = p1[i] = 0ull;
           }
         } else {
@@ -781,13 +779,20 @@ __global__ void __launch_bounds__(max_threads(RPL), 1) sketch_dense_kernel(const
             a0[i] = a1[i] = 0.f;
           }
         }
-        if (HW) {  // both halves end with the same sum (FP32 addition commutes)
+        if (HW) {
+          // half h finishes rows h*EPR.. of its pair: it sends the other
+          // half's rows and adds what it receives (FP32 addition commutes,
+          // so the sum is the one either half would form)
 #pragma unroll
-          for (int i = 0; i < RPL; ++i) ys[i] += __shfl_xor_sync(0xffffffffu, ys[i], 16);
+          for (int k = 0; k < EPR; ++k) {
+            const float mine = h ? ys[EPR + k] : ys[k];
+            const float other = __shfl_xor_sync(0xffffffffu, h ? ys[k] : ys[EPR + k], 16);
+            ys[k] = mine + other;
+          }
         }
 #pragma unroll
         for (int k = 0; k < EPR; ++k) {
-          const float y = HW ? (h ? ys[EPR + k] : ys[k]) : ys[k];
+          const float y = ys[k];
           const int ri = re0 + k;  // the row in the tile
           const int64_t row = row0 + ri;
           int code;
