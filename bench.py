@@ -2,7 +2,8 @@
 
 Step = one pass of the whole indexing path over one batch: CS/HCS hashing of
 all L tables (with the FP64 boundary recheck and key fold) -> per-table
-stable radix sort of (key, id) -> bucket segmentation, i.e. lsh_index_rebuild
+stable sort of (key, id) (the bucket sort: one global radix pass, buckets
+finished on chip) -> bucket segmentation, i.e. lsh_index_rebuild
 on a resident batch.  Workload (default): 1,000,000 x 960 FP32 points from a
 64-component Gaussian mixture (the Gist-shaped set), CS-E2LSH, m = 64, L = 50,
 w = 4.  Inputs (3.84 GB) are larger than L2 (129 MB), so no flush is needed.
@@ -1004,7 +1005,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "kind": fam_args["kind"], "n_per_gpu": n, "d": d,
                        "m": m, "L": L, "w": fam_args["w"],
-                       "step": "lsh_index_rebuild: hash (FP32 + FP64 recheck) + radix sort + buckets",
+                       "step": "lsh_index_rebuild: hash (FP32 + FP64 recheck) + bucket sort + segmentation",
                        "l2": "inputs larger than L2 (%.2f GB per GPU)" % x_gb},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
