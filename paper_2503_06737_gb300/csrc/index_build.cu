@@ -1,13 +1,14 @@
 // index_build.cu -- the L hash tables of the (m, tau)-amplified LSH scheme
 // (Sec. 3.1): every point is stored in the bucket of its key in each table.
 //
-// Per table the (key, id) pairs are put in (key, id) order by a stable LSD
-// radix sort over the 64-bit key, 8 bits per pass (ids start in ascending
-// order, so stability gives ascending ids inside a bucket), and the sorted
-// keys are cut into buckets: distinct keys ascending and the start offset of
-// each bucket.  All L tables are sorted by the same launches (grid.y = table).
+// Per table the (key, id) pairs are put in (key, id) order by a stable sort
+// (ids start in ascending order, so stability gives ascending ids inside a
+// bucket), and the sorted keys are cut into buckets: distinct keys ascending
+// and the start offset of each bucket.  All L tables are sorted by the same
+// launches (grid.y = table).  Two sorts give the same order: the LSD radix
+// sort over the 64-bit key, 8 bits per pass, and the bucket sort below.
 //
-// One pass = three kernels:
+// One LSD pass = three kernels:
 //   histogram  per (table, tile of 4096 keys): digit counts, digit-major;
 //   scan       per table: exclusive scan over (digit, tile) -> global offsets;
 //   scatter    per (table, tile): stable ranks inside the tile from warp
@@ -19,11 +20,11 @@
 // reduction finds the bits on which a table's keys differ; one pass on the 8
 // highest of them cuts the table into 256 buckets (about n / 256 keys each
 // for hashed keys), and one CTA per (bucket, table) finishes the stable sort
-// -- on chip when the bucket has at most kBCap keys (a counting pass on the
-// next 8 bits, then comparisons inside the small groups it leaves), else by
-// counting passes on the lower digits through global memory in sub-tiles of
-// kBCap, skipping digits on which the table's, or the bucket's, keys all
-// agree.  The same (key, id) order as the eight global passes, at one global
+// -- on chip when the bucket has at most kBCap keys and the counting pass
+// on the next 8 bits leaves groups of at most kGroupMax (then comparisons
+// inside each group place its keys), else by counting passes on the lower
+// digits through global memory in sub-tiles of kBCap, skipping digits on
+// which the table's, or the bucket's, keys all agree.  The same (key, id) order as the eight global passes, at one global
 // pass plus one read and one write of every pair.
 #include <cuda_runtime.h>
 #include <stdint.h>
